@@ -1,0 +1,97 @@
+"""The pins must fail on plausible mistakes.
+
+Each case plants one mistake in the oracle (monkeypatched, CPU only) and
+checks that at least one pin of the paper-form / brute-force / library
+suites then fails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.dctf_oracle as od
+from tests import test_oracle_dct as t_dct
+from tests import test_oracle_filter as t_filt
+from tests import test_oracle_paper_form as t_paper
+
+_orig_build_H = od.build_H
+_orig_dct = od.dct_matrix
+
+
+def h_convolution(w, anchor, n, boundary):
+    mh, mw = np.shape(w)
+    return _orig_build_H(np.asarray(w)[::-1, ::-1], (mh - 1 - anchor[0], mw - 1 - anchor[1]), n, boundary)
+
+
+def h_transposed(w, anchor, n, boundary):
+    return _orig_build_H(w, anchor, n, boundary).T
+
+
+def h_swapped_anchor(w, anchor, n, boundary):
+    w = np.asarray(w)
+    if w.shape[0] == w.shape[1]:
+        return _orig_build_H(w, (anchor[1], anchor[0]), n, boundary)
+    return _orig_build_H(w, anchor, n, boundary)
+
+
+def h_dropped_term(w, anchor, n, boundary):
+    w = np.array(w, dtype=float)
+    w[-1, -1] = 0.0
+    return _orig_build_H(w, anchor, n, boundary)
+
+
+def h_wrong_boundary(w, anchor, n, boundary):
+    return _orig_build_H(w, anchor, n, 1 - boundary)
+
+
+def dct_no_alpha0(n):
+    c = _orig_dct(n).copy()
+    c[0] *= math.sqrt(2.0)
+    return c
+
+
+def dct_transposed(n):
+    return _orig_dct(n).T.copy()
+
+
+MUTANTS = {
+    "convolution": ("build_H", h_convolution),
+    "transposed_H": ("build_H", h_transposed),
+    "swapped_anchor": ("build_H", h_swapped_anchor),
+    "dropped_term": ("build_H", h_dropped_term),
+    "wrong_boundary": ("build_H", h_wrong_boundary),
+    "dct_alpha": ("dct_matrix", dct_no_alpha0),
+    "dct_transposed": ("dct_matrix", dct_transposed),
+}
+
+
+def _pins():
+    sym = t_paper.load_symbolic()
+    return [
+        lambda: t_paper.test_paper_equations_equal_oracle_operator(sym, oracle.ZERO),
+        lambda: t_paper.test_paper_equations_equal_oracle_operator(sym, oracle.REPLICATE),
+        lambda: t_filt.test_spatial_filter_brute_force_4x4(oracle.REPLICATE, 2, 3),
+        lambda: t_filt.test_operator_route_equals_spatial_route_fp64(),
+        lambda: t_dct.test_dct_matrix_matches_scipy(8),
+        lambda: t_dct.test_blockwise_dct_matches_scipy(8),
+    ]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, monkeypatch):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(od, attr, fn)
+    monkeypatch.setattr(oracle, attr, fn)
+    failures = 0
+    for pin in _pins():
+        try:
+            pin()
+        except AssertionError:
+            failures += 1
+    assert failures > 0, f"mutant {name} passed every pin"
+
+
+def test_unmutated_oracle_passes_every_pin():
+    for pin in _pins():
+        pin()
