@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of block-DCT-domain filtering on the 4096x4096 headline workload.
+
+One step = one pass of the whole path over one image: rebuild the operator
+on the device in FP64 for the step's mask (H, M = K H K^T, FP16 pieces) and
+apply it to all 262,144 8x8 blocks (FP32 coefficients in HBM -> filtered
+FP32 coefficients in HBM).  Each step runs as two CUDA-graph replays (build,
+apply) on one stream, with CUDA events around the apply to time that kernel
+live.  Inputs rotate over 8 buffer pairs (1.07 GB > 129 MB of L2), so no step
+reads its input from L2.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
+the host cores instead (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+METRIC = "filtered 8x8 blocks/s, % HBM peak (TC-split vs FP32, uint8-exact); p99 latency"
+UNIT = "blocks/s"
+WORKLOAD = "4096x4096 uint8 image, 262144 8x8 blocks, FP32 coefficients, random asymmetric 5x5 mask anchor (1,3), border replication"
+BYTES_PER_BLOCK = 512          # 256 B of FP32 coefficients in + 256 B out
+ROTATE = 8
+
+# ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
+# the full workload, valid only for the kernel source it was taken from.
+NCU_TRAFFIC = {}               # {sha1 of apply_tc.cu: bytes per launch}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", choices=["dctf", "reference"], default="dctf")
+    p.add_argument("--size", type=int, default=4096, help="image side (multiple of 8)")
+    p.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps, capped at 500")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-simt", action="store_true", help="skip the FP32 CUDA-core comparison")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_1710_07193_gb300", "csrc", "apply_tc.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 100 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        win = [p for (t, p) in self.samples if t0 - 0.15 <= t <= t1 + 0.15]
+        if not win:
+            win = [p for (_, p) in self.samples[-3:]]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(p[0]) for p in win if p[0].replace(".", "").isdigit()]
+        mx = [float(p[1]) for p in win if p[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in win for i in range(4) if p[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(win),
+                "power_w_max": max((float(p[2]) for p in win
+                                    if p[2].replace(".", "").isdigit()), default=None)}
+
+
+# ------------------------------------------------------------ reference arm
+def cpu_oracle_sample(job, x, n_sample: int, reps_target_s: float):
+    """Time the FP64 oracle (operator build + apply) on a sample of blocks."""
+    import oracle
+    sl = x[:n_sample].astype(np.float64)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        m = oracle.build_M(job.mask, job.anchor, 8, job.boundary)
+        oracle.apply_M(m, sl)
+        reps += 1
+        if time.perf_counter() - t0 >= reps_target_s:
+            break
+    dt = time.perf_counter() - t0
+    return reps * n_sample / dt, reps, dt
+
+
+def oracle_coefficients(job):
+    import oracle
+    return oracle.dct2_blocks(oracle.image_to_blocks(job.image, 8)).astype(np.float32)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    job = datagen.headline_job(args.size, args.size)
+    x = oracle_coefficients(job)
+    nb = x.shape[0]
+    sample = min(nb, 8192)
+    m = None
+    for i in range(args.warmup):
+        m = oracle.build_M(job.mask, job.anchor, 8, job.boundary)
+        oracle.apply_M(m, x[(i * sample) % nb:(i * sample) % nb + sample].astype(np.float64))
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        lo = (i * sample) % nb
+        m = oracle.build_M(job.mask, job.anchor, 8, job.boundary)
+        oracle.apply_M(m, x[lo:lo + sample].astype(np.float64))
+    dt = time.perf_counter() - t0
+    value = args.steps * sample / dt
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "step_sample_blocks": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} contiguous blocks of the workload per step "
+                                   f"(operator build + apply, numpy FP64, BLAS threads default)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_dctf(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1710_07193_gb300 as lib
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib.load()
+
+    job = datagen.headline_job(args.size, args.size)
+    h, w = job.image.shape
+    nb = (h // 8) * (w // 8)
+    stream = torch.cuda.current_stream()
+
+    # inputs: coefficients made on the device by the library's forward DCT
+    img_d = torch.from_numpy(job.image).to(dev)
+    x0 = torch.empty((nb, 64), dtype=torch.float32, device=dev)
+    lib.forward_dct(img_d, h, w, 8, x0)
+    xs = [x0.clone() for _ in range(ROTATE)]
+    ys = [torch.empty_like(x0) for _ in range(ROTATE)]
+    del img_d
+    op = lib.build_operator(job.mask, job.anchor, 8, job.boundary)
+    torch.cuda.synchronize()
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            fn()                                   # warm (attribute set-up) outside capture
+            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                fn()
+        stream.wait_stream(s)
+        torch.cuda.synchronize()
+        return g
+
+    g_build = capture(lambda: op.rebuild(job.mask, job.anchor, job.boundary))
+
+    def graphs_for(prec):
+        op.set_precision(prec)
+        return [capture(lambda j=j: lib.apply(op, xs[j], nb, ys[j])) for j in range(ROTATE)]
+
+    g_apply = graphs_for(lib.F16X3)
+    g_simt = None if args.no_simt else graphs_for(lib.FP32_SIMT)
+    op.set_precision(lib.F16X3)
+
+    def timed(graphs, steps, warmup, sampler=None):
+        for i in range(warmup):
+            g_build.replay()
+            graphs[i % ROTATE].replay()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        start.record(stream)
+        for i in range(steps):
+            g_build.replay()
+            ev_a[i].record(stream)
+            graphs[i % ROTATE].replay()
+            ev_b[i].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        if ws > 1:
+            dist.barrier()
+        total_ms = start.elapsed_time(end)
+        apply_ms = [a.elapsed_time(b) for a, b in zip(ev_a, ev_b)]
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), statistics.mean(apply_ms), statistics.median(apply_ms), (t0, t1)
+
+    gpu_id = f"GPU-{torch.cuda.get_device_properties(dev).uuid}" if hasattr(
+        torch.cuda.get_device_properties(dev), "uuid") else str(local)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    total_ms, apply_mean, apply_med, (t0, t1) = timed(g_apply, args.steps, args.warmup)
+    simt = None
+    if g_simt is not None:
+        s_total, s_mean, s_med, _ = timed(g_simt, args.steps, args.warmup)
+        simt = {"value": ws * nb * args.steps / (s_total / 1e3), "ms_per_step": s_total / args.steps,
+                "apply_us": 1e3 * s_mean,
+                "apply_GBps": BYTES_PER_BLOCK * nb / (s_mean / 1e3) / 1e9}
+    time.sleep(0.2)
+    sampler.stop()
+    clocks = sampler.summary(t0, t1)
+
+    # end to end through the public host-buffer call: H2D + build + apply + D2H
+    e2e_steps = args.e2e_steps or min(args.steps, 500)
+    hin = x0.cpu().pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(3):
+        op.rebuild(job.mask, job.anchor, job.boundary)
+        lib.apply_host(op, hin, nb, hout)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        op.rebuild(job.mask, job.anchor, job.boundary)
+        lib.apply_host(op, hin, nb, hout)
+    e_dt = time.perf_counter() - e0
+    e2e = {"value": ws * nb * e2e_steps / e_dt, "unit": UNIT,
+           "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
+           "steps": e2e_steps, "path": "dctf_apply_host, pinned host buffers, 64k-block chunks on 2 streams"}
+
+    status = op.status()
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_BLOCK * nb / (apply_mean / 1e3) / 1e9
+    traffic = NCU_TRAFFIC.get(kernel_source_hash())
+    line = {
+        "metric": METRIC, "value": ws * nb * args.steps / (total_ms / 1e3), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f16x3 tensor-core split, fp32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "blocks_per_step": nb, "precision": "F16X3",
+                   "step": "operator rebuild (FP64, 2 kernels) + apply (1 kernel)",
+                   "l2": f"{ROTATE} rotating input/output buffer pairs, "
+                         f"{ROTATE * 2 * nb * 256 / 1e9:.2f} GB > L2",
+                   "parallelism": f"dp{ws} (independent images, no collective)"},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "apply_tc_f16x3_n8", "apply_us_mean": 1e3 * apply_mean,
+                     "apply_us_median": 1e3 * apply_med},
+        "fp32_simt": simt,
+        "e2e": e2e,
+        "clocks": clocks,
+        "device_status": status,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        x_host = x0.cpu().numpy()
+        v, reps, dt = cpu_oracle_sample(job, x_host, 65536, 8.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{reps} x (operator build + apply to 65536 of the "
+                                          f"262144 blocks), {dt:.1f} s, numpy FP64"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    op.release()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_dctf(args)
+
+
+if __name__ == "__main__":
+    main()

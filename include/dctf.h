@@ -1,0 +1,175 @@
+/*
+ * dctf.h - C ABI of the GB300 block-DCT-domain filtering library (libdctf.so).
+ *
+ * The library applies a 2-D filter mask to the N x N block-DCT coefficients
+ * of an image without returning to pixels.  The whole filter (mask, anchor,
+ * per-block zero padding or border replication) is folded into one N^2 x N^2
+ * operator M = (C kron C) H (C kron C)^T, built on the GPU in FP64 once per
+ * mask, and then y_b = M x_b is computed for every block b.
+ *
+ *   Paper: "Block DCT filtering using vector processing" (arXiv 1710.07193).
+ *   Sec. II.A, Eq. 1-3 : orthonormal DCT-II, BLOCK = C block C^T.
+ *   Sec. II.B, Eq. 5-11: zero-padded filtering as sums of matrix products.
+ *   Sec. II.C, Eq. 13-20: border replication added as further products.
+ *   Eq. 7              : a spatial product moves to the DCT domain by
+ *                        conjugation with C; for the vectorised block the
+ *                        whole filter H becomes M = K H K^T, K = C kron C.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - N (block side) is 4, 8 or 16; a block has N2 = N*N coefficients.
+ *  - Coefficient (u, v) of a block (u vertical, v horizontal frequency) is
+ *    element u*N + v; a batch is [nblocks][N2], contiguous, blocks in any
+ *    order (raster order of the image by convention).
+ *  - The mask is a row-major mh x mw array of doubles with 1 <= mh, mw <= N;
+ *    anchor = {row, col} is the mask entry over the output pixel.  The filter
+ *    is a correlation: out(i,j) = sum_{r,c} w[r][c] x(i+r-ar, j+c-ac), the
+ *    reading of Eq. 5 that the printed matrices of Eq. 6-18 implement.
+ *    Each block is padded on its own (pixels of other blocks are never read).
+ *  - Device pointers must be 16-byte aligned.  nblocks == 0 is a no-op.
+ *  - Calls taking a stream are asynchronous on it; their return value covers
+ *    argument checks and launch errors only.  Device-side failures (a bounded
+ *    wait that ran out) are latched in the operator's status word, read with
+ *    dctf_operator_status.
+ *  - Every call returns DCTF_OK or an error code, never aborts; the message
+ *    of the last error on the calling thread is dctf_last_error().
+ *  - The caller owns every coefficient buffer; an operator owns its device
+ *    memory until dctf_release_operator.
+ */
+#ifndef DCTF_H
+#define DCTF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *dctf_stream_t;
+
+typedef enum {
+    DCTF_OK = 0,
+    DCTF_EINVAL = 1,        /* bad argument: nothing was launched          */
+    DCTF_ENOMEM = 2,        /* device or host allocation failed            */
+    DCTF_ECUDA = 3,         /* a CUDA runtime call failed                  */
+    DCTF_EBUDGET = 4,       /* request larger than the server's HBM budget */
+    DCTF_ETIMEOUT = 5,      /* a bounded wait ran out (host or device)     */
+    DCTF_EUNSUPPORTED = 6   /* valid but not supported (e.g. N, precision) */
+} dctf_status;
+
+typedef enum { DCTF_ZERO = 0, DCTF_REPLICATE = 1 } dctf_boundary;
+
+/* Arithmetic of dctf_apply.  Every variant accumulates in FP32 and applies
+ * the input DC coefficient's contribution as a separate FP32 rank-1 term.
+ *  FP32_SIMT : plain FP32 FMA on CUDA cores (comparison kernel).
+ *  F16X3     : tcgen05 tensor cores, FP16 hi/lo split of x and M,
+ *              hi*hi + hi*lo + lo*hi.  |x| must stay below 65504.
+ *  TF32X3    : tcgen05, TF32 hi/lo split, three products (not yet built).
+ *  BF16X6    : tcgen05, three BF16 pieces, six products (not yet built). */
+typedef enum {
+    DCTF_FP32_SIMT = 0,
+    DCTF_F16X3 = 1,
+    DCTF_BF16X6 = 2,
+    DCTF_TF32X1 = 3,
+    DCTF_TF32X3 = 4
+} dctf_precision;
+
+typedef struct dctf_operator dctf_operator;
+
+/* Build the operator for one mask (Sec. II.B-C; M = K H K^T by Eq. 7).
+ *  mask     host, row-major mh*mw doubles, copied (not kept).
+ *  anchor   host {row, col}, 0-based inside the mask.
+ *  n        4, 8 or 16.   boundary  DCTF_ZERO or DCTF_REPLICATE.
+ *  stream   the FP64 build kernels run on it; *out may be used on that
+ *           stream at once, on others after synchronising with it.
+ * Allocates device memory on the current device (cudaMalloc).  The
+ * precision starts as DCTF_F16X3 where tensor-core kernels exist for n,
+ * else DCTF_FP32_SIMT.  EINVAL for a bad mask/anchor/n/boundary/out. */
+dctf_status dctf_build_operator(const double *mask, int mh, int mw,
+                                const int anchor[2], int n,
+                                dctf_boundary boundary, dctf_stream_t stream,
+                                dctf_operator **out);
+
+/* Rebuild an existing operator for a new mask of the same n, in place, on
+ * `stream` (the paper's point that the prepared matrices are simply rebuilt
+ * when the mask changes, Sec. I and IV).  Allocates nothing; the mask travels
+ * in the kernel parameters, so the call can be captured in a CUDA graph.
+ * Work already queued on other streams that reads the operator must finish
+ * first. */
+dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask,
+                                  int mh, int mw, const int anchor[2],
+                                  dctf_boundary boundary, dctf_stream_t stream);
+
+/* Choose the arithmetic of later dctf_apply calls.  EUNSUPPORTED if no
+ * kernel exists for (n, p).  Not synchronised with concurrent applies. */
+dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p);
+
+/* Read back (synchronously, after the build finished) the FP64 operator M
+ * (n2*n2, row-major: row = output coefficient) and, if H_host is not NULL,
+ * the spatial operator H (n2*n2, row = output pixel i*n+j).  For tests. */
+dctf_status dctf_operator_download(const dctf_operator *op, double *M_host,
+                                   double *H_host);
+
+/* Device status word of the operator: 0 when every kernel that used it ran
+ * to completion; else the code of the first bounded wait that ran out
+ * (bits 0-7 the role, bits 8-31 the tile).  Synchronises the device.  With
+ * clear != 0 the word is reset to 0 afterwards. */
+dctf_status dctf_operator_status(dctf_operator *op, uint32_t *code, int clear);
+
+void dctf_release_operator(dctf_operator *op);
+
+/* y_b = M x_b for b < nblocks (Eq. 11 zero padding, Eq. 20 replication).
+ *  coeffs, out  device [nblocks][n2] FP32; out == coeffs (in place) allowed,
+ *               any other overlap is not.
+ * Arithmetic per dctf_operator_set_precision. */
+dctf_status dctf_apply(const dctf_operator *op, const float *coeffs,
+                       int64_t nblocks, float *out, dctf_stream_t stream);
+
+/* As dctf_apply, with FP64 input coefficients (FP32 output), FP32 SIMT
+ * arithmetic; for the small FP64-coefficient workload. */
+dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs,
+                             int64_t nblocks, float *out,
+                             dctf_stream_t stream);
+
+/* End-to-end call for callers holding the data in HOST memory: copies
+ * host_in to the device, applies, copies the result to host_out, in chunks
+ * pipelined over two internal streams and device buffers owned by the
+ * operator.  The internal streams are blocking streams: the copies start
+ * after work already queued on the legacy default stream (e.g. a rebuild).
+ * Synchronous: returns after host_out is written.  host_in and host_out
+ * should be pinned (cudaHostAlloc) for full speed.  The first call allocates
+ * the staging buffers (4 x 16 MB at n = 8). */
+dctf_status dctf_apply_host(dctf_operator *op, const float *host_in,
+                            int64_t nblocks, float *host_out);
+
+/* Blockwise forward DCT of a uint8 image (Sec. II.A, Eq. 1): block (by, bx)
+ * in raster order b = by*(width/n) + bx gets BLOCK = C block C^T, written as
+ * coeffs[b][u*n + v].  image: device, height x width bytes, row pitch `pitch`
+ * >= width; height and width multiples of n.  FP64 arithmetic; the FP32
+ * variant rounds the result once.  Asynchronous on `stream`. */
+dctf_status dctf_forward_dct(const uint8_t *image, int height, int width,
+                             int64_t pitch, int n, float *coeffs,
+                             dctf_stream_t stream);
+dctf_status dctf_forward_dct_f64(const uint8_t *image, int height, int width,
+                                 int64_t pitch, int n, double *coeffs,
+                                 dctf_stream_t stream);
+
+/* Inverse of dctf_forward_dct followed by the uint8 conversion of Sec. III:
+ * block = C^T BLOCK C (Eq. 3), rounded half away from zero and saturated to
+ * [0, 255], written into a device image of the given pitch.  FP64 inside. */
+dctf_status dctf_inverse_dct_u8(const float *coeffs, int height, int width,
+                                int n, uint8_t *image, int64_t pitch,
+                                dctf_stream_t stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dctf_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int dctf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCTF_H */

@@ -1,0 +1,177 @@
+// Plain FP32 CUDA-core apply: y_b = M x_b (Eq. 11 / Eq. 20) with FP32 FMA.
+//
+// The comparison kernel of the library.  A CTA keeps a tile of TB blocks
+// resident in shared memory (so in-place filtering is safe: every input of
+// the tile is read before any output of it is written) and sweeps the
+// outputs in TN-wide chunks and the inputs in TK-wide chunks of M.  Each
+// thread owns an RB x RN register tile (blocks strided by TB/RB, outputs by
+// TN/RN, which keeps the 16-byte shared loads of a warp on distinct banks).
+// The input DC coefficient x_b[0] is left out of the running sums and added
+// last as M[:,0] x_b[0]: it is the largest coefficient by far, and adding it
+// once to an accumulator of the AC terms keeps the rounding error of the
+// sums near one ulp of the output instead of growing with the DC magnitude.
+#include "dctf_internal.cuh"
+
+namespace dctf {
+namespace {
+
+template <typename Tin> __device__ inline float4 load4(const Tin *p);
+template <> __device__ inline float4 load4<float>(const float *p) {
+  return __ldg(reinterpret_cast<const float4 *>(p));
+}
+template <> __device__ inline float4 load4<double>(const double *p) {
+  double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+template <int N2, int TB, int TN, int TK, int RB, int RN>
+struct SimtCfg {
+  static constexpr int kThreads = (TB / RB) * (TN / RN);
+  static constexpr int kXP = N2 + 4;        // X row pitch (floats)
+  static constexpr int kMP = TK + 4;        // M chunk row pitch
+  static constexpr int kYP = TN + 4;        // Y staging pitch
+  static constexpr bool kMResident = (TN == N2 && TK == N2);
+  static constexpr bool kYAliasX = (TN == N2);
+  static constexpr int kXFloats = TB * kXP;
+  static constexpr int kMFloats = TN * kMP;
+  static constexpr int kYFloats = kYAliasX ? 0 : TB * kYP;
+  static constexpr size_t kSmem = (size_t)(kXFloats + kMFloats + kYFloats + TB) * 4;
+  static_assert(kThreads == 128, "128 threads per CTA");
+  static_assert(!kYAliasX || TB * kYP <= kXFloats, "Y staging must fit in X");
+};
+
+template <typename Tin, int N2, int TB, int TN, int TK, int RB, int RN>
+__global__ void __launch_bounds__(128)
+apply_simt_kernel(const float *__restrict__ M32, const float *__restrict__ Mdc,
+                  const Tin *__restrict__ x, int64_t nblocks, float *y) {
+  using Cfg = SimtCfg<N2, TB, TN, TK, RB, RN>;
+  constexpr int TPB = TB / RB;   // thread rows (blocks)
+  constexpr int TPN = TN / RN;   // thread columns (outputs)
+  extern __shared__ __align__(16) float smem[];
+  float *Xs = smem;
+  float *Ms = Xs + Cfg::kXFloats;
+  float *Ys = Cfg::kYAliasX ? Xs : Ms + Cfg::kMFloats;
+  float *x0s = Ms + Cfg::kMFloats + Cfg::kYFloats;
+  const int t = threadIdx.x, tb = t / TPN, tn = t % TPN;
+  const int64_t ntiles = (nblocks + TB - 1) / TB;
+
+  if (Cfg::kMResident) {
+    for (int idx = t; idx < N2 * N2 / 4; idx += 128) {
+      int r = idx / (N2 / 4), c4 = idx % (N2 / 4);
+      *reinterpret_cast<float4 *>(&Ms[r * Cfg::kMP + 4 * c4]) =
+          __ldg(reinterpret_cast<const float4 *>(M32 + (size_t)r * N2) + c4);
+    }
+  }
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t b0 = tile * TB;
+    __syncthreads();   // previous tile's readers of Xs / Ys are done
+    for (int idx = t; idx < TB * N2 / 4; idx += 128) {
+      int r = idx / (N2 / 4), c4 = idx % (N2 / 4);
+      int64_t b = b0 + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b < nblocks) v = load4<Tin>(x + b * N2 + 4 * c4);
+      if (c4 == 0) { x0s[r] = v.x; v.x = 0.f; }
+      *reinterpret_cast<float4 *>(&Xs[r * Cfg::kXP + 4 * c4]) = v;
+    }
+    for (int n0 = 0; n0 < N2; n0 += TN) {
+      float acc[RB][RN];
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) acc[i][j] = 0.f;
+      for (int k0 = 0; k0 < N2; k0 += TK) {
+        if (!Cfg::kMResident) {
+          __syncthreads();
+          for (int idx = t; idx < TN * TK / 4; idx += 128) {
+            int r = idx / (TK / 4), c4 = idx % (TK / 4);
+            *reinterpret_cast<float4 *>(&Ms[r * Cfg::kMP + 4 * c4]) =
+                __ldg(reinterpret_cast<const float4 *>(M32 + (size_t)(n0 + r) * N2 + k0) + c4);
+          }
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int k4 = 0; k4 < TK; k4 += 4) {
+          float4 xa[RB], ma[RN];
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+            xa[i] = *reinterpret_cast<const float4 *>(&Xs[(tb + TPB * i) * Cfg::kXP + k0 + k4]);
+#pragma unroll
+          for (int j = 0; j < RN; ++j)
+            ma[j] = *reinterpret_cast<const float4 *>(&Ms[(tn + TPN * j) * Cfg::kMP + k4]);
+#pragma unroll
+          for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int j = 0; j < RN; ++j) {
+              acc[i][j] = fmaf(xa[i].x, ma[j].x, acc[i][j]);
+              acc[i][j] = fmaf(xa[i].y, ma[j].y, acc[i][j]);
+              acc[i][j] = fmaf(xa[i].z, ma[j].z, acc[i][j]);
+              acc[i][j] = fmaf(xa[i].w, ma[j].w, acc[i][j]);
+            }
+        }
+      }
+      // the DC input term, last (see the file comment)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) {
+        float md = __ldg(Mdc + n0 + tn + TPN * j);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) acc[i][j] = fmaf(md, x0s[tb + TPB * i], acc[i][j]);
+      }
+      __syncthreads();   // all reads of Xs (aliased by Ys) / Ys are done
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) Ys[(tb + TPB * i) * Cfg::kYP + tn + TPN * j] = acc[i][j];
+      __syncthreads();
+      for (int idx = t; idx < TB * TN / 4; idx += 128) {
+        int r = idx / (TN / 4), c4 = idx % (TN / 4);
+        int64_t b = b0 + r;
+        if (b < nblocks)
+          *reinterpret_cast<float4 *>(y + b * N2 + n0 + 4 * c4) =
+              *reinterpret_cast<const float4 *>(&Ys[r * Cfg::kYP + 4 * c4]);
+      }
+    }
+  }
+}
+
+template <typename Tin, int N2, int TB, int TN, int TK, int RB, int RN>
+cudaError_t launch_cfg(const dctf_operator *op, const Tin *x, int64_t nblocks, float *y,
+                       cudaStream_t s) {
+  using Cfg = SimtCfg<N2, TB, TN, TK, RB, RN>;
+  auto kern = apply_simt_kernel<Tin, N2, TB, TN, TK, RB, RN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg::kSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, Cfg::kSmem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t ntiles = (nblocks + TB - 1) / TB;
+  int64_t grid = (int64_t)per_sm * sm_count(op->device);
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, 128, Cfg::kSmem, s>>>(op->d_M32, op->d_Mdc, x, nblocks, y);
+  return cudaGetLastError();
+}
+
+template <typename Tin>
+cudaError_t dispatch(const dctf_operator *op, const Tin *x, int64_t nblocks, float *y,
+                     cudaStream_t s) {
+  switch (op->n) {
+    case 4:  return launch_cfg<Tin, 16, 128, 16, 16, 8, 2>(op, x, nblocks, y, s);
+    case 8:  return launch_cfg<Tin, 64, 128, 64, 64, 8, 8>(op, x, nblocks, y, s);
+    case 16: return launch_cfg<Tin, 256, 32, 128, 64, 4, 8>(op, x, nblocks, y, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_apply_simt(const dctf_operator *op, const float *x, const double *x64,
+                              int64_t nblocks, float *y, cudaStream_t s) {
+  if (x64 != nullptr) return dispatch<double>(op, x64, nblocks, y, s);
+  return dispatch<float>(op, x, nblocks, y, s);
+}
+
+}  // namespace dctf

@@ -1,0 +1,269 @@
+// C-ABI entry points: argument checks, operator lifetime, dispatch.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "dctf_internal.cuh"
+
+namespace dctf {
+
+static thread_local std::string g_last_error;
+
+dctf_status set_error(dctf_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+dctf_status cuda_error(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(DCTF_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(DCTF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int sm_count(int device) {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  std::lock_guard<std::mutex> lock(mu);
+  if (device < 0 || device >= 64) return 0;
+  if (cache[device] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    cache[device] = v;
+  }
+  return cache[device];
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+static dctf_status check_mask(const double *mask, int mh, int mw, const int anchor[2],
+                              int n, int boundary, MaskParams *mp) {
+  if (n != 4 && n != 8 && n != 16)
+    return set_error(DCTF_EINVAL, "block size n=%d: must be 4, 8 or 16", n);
+  if (mask == nullptr || anchor == nullptr)
+    return set_error(DCTF_EINVAL, "mask and anchor must not be NULL");
+  if (mh < 1 || mw < 1 || mh > n || mw > n)
+    return set_error(DCTF_EINVAL, "mask %dx%d must fit in the %dx%d block", mh, mw, n, n);
+  if (anchor[0] < 0 || anchor[0] >= mh || anchor[1] < 0 || anchor[1] >= mw)
+    return set_error(DCTF_EINVAL, "anchor (%d,%d) outside the %dx%d mask", anchor[0], anchor[1], mh, mw);
+  if (boundary != DCTF_ZERO && boundary != DCTF_REPLICATE)
+    return set_error(DCTF_EINVAL, "boundary %d: must be DCTF_ZERO or DCTF_REPLICATE", boundary);
+  memset(mp, 0, sizeof *mp);
+  for (int k = 0; k < mh * mw; ++k) {
+    if (!std::isfinite(mask[k])) return set_error(DCTF_EINVAL, "mask entry %d is not finite", k);
+    mp->w[k] = mask[k];
+  }
+  mp->mh = mh; mp->mw = mw; mp->ar = anchor[0]; mp->ac = anchor[1];
+  mp->n = n; mp->boundary = boundary;
+  return DCTF_OK;
+}
+
+// Power of two s with |M 2^s| <= 2^14: ||M||_2 = ||H||_2 <= sum|w| * n, a
+// bound on every entry, so the FP16 pieces neither overflow nor lose the lo
+// part to subnormals.
+static int f16_scale_exponent(const MaskParams &mp) {
+  double s = 0.0;
+  for (int k = 0; k < mp.mh * mp.mw; ++k) s += fabs(mp.w[k]);
+  double bound = s * mp.n;
+  if (bound <= 0.0) return 0;
+  int e = 14 - (int)ceil(log2(bound));
+  return e < -24 ? -24 : (e > 24 ? 24 : e);
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace dctf
+
+using namespace dctf;
+
+extern "C" {
+
+int dctf_version(void) { return 100; }
+
+const char *dctf_last_error(void) { return g_last_error.c_str(); }
+
+dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int anchor[2],
+                                int n, dctf_boundary boundary, dctf_stream_t stream,
+                                dctf_operator **out) {
+  if (out == nullptr) return set_error(DCTF_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  MaskParams mp;
+  dctf_status st = check_mask(mask, mh, mw, anchor, n, boundary, &mp);
+  if (st != DCTF_OK) return st;
+
+  dctf_operator *op = new (std::nothrow) dctf_operator();
+  if (op == nullptr) return set_error(DCTF_ENOMEM, "host allocation of the operator failed");
+  DCTF_CUDA(cudaGetDevice(&op->device));
+  op->n = n; op->n2 = n * n;
+  const size_t n2 = op->n2, sq = n2 * n2;
+  const bool pieces = tc_supported(n, DCTF_F16X3);
+  size_t off = 0, o_M64, o_H64, o_G64, o_M32, o_Mdc, o_f16 = 0, o_err;
+  o_M64 = off; off = align_up(off + sq * 8, 1024);
+  o_H64 = off; off = align_up(off + sq * 8, 1024);
+  o_G64 = off; off = align_up(off + sq * 8, 1024);
+  o_M32 = off; off = align_up(off + sq * 4, 1024);
+  o_Mdc = off; off = align_up(off + n2 * 4, 1024);
+  if (pieces) { o_f16 = off; off = align_up(off + 2 * sq * 2, 1024); }
+  o_err = off; off = align_up(off + 256, 1024);
+  cudaError_t e = cudaMalloc(&op->d_base, off);
+  if (e != cudaSuccess) { delete op; return cuda_error(e, "cudaMalloc(operator)"); }
+  op->bytes = off;
+  char *b = static_cast<char *>(op->d_base);
+  op->d_M64 = reinterpret_cast<double *>(b + o_M64);
+  op->d_H64 = reinterpret_cast<double *>(b + o_H64);
+  op->d_G64 = reinterpret_cast<double *>(b + o_G64);
+  op->d_M32 = reinterpret_cast<float *>(b + o_M32);
+  op->d_Mdc = reinterpret_cast<float *>(b + o_Mdc);
+  op->d_f16 = pieces ? reinterpret_cast<__half *>(b + o_f16) : nullptr;
+  op->d_err = reinterpret_cast<uint32_t *>(b + o_err);
+  op->precision = pieces ? DCTF_F16X3 : DCTF_FP32_SIMT;
+
+  e = cudaMemsetAsync(op->d_err, 0, 256, stream);
+  if (e == cudaSuccess && pieces) e = cudaMemsetAsync(op->d_f16, 0, 2 * sq * 2, stream);
+  if (e != cudaSuccess) { dctf_release_operator(op); return cuda_error(e, "cudaMemsetAsync"); }
+  st = dctf_operator_rebuild(op, mask, mh, mw, anchor, boundary, stream);
+  if (st != DCTF_OK) { dctf_release_operator(op); return st; }
+  *out = op;
+  return DCTF_OK;
+}
+
+dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask, int mh, int mw,
+                                  const int anchor[2], dctf_boundary boundary,
+                                  dctf_stream_t stream) {
+  if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
+  MaskParams mp;
+  dctf_status st = check_mask(mask, mh, mw, anchor, op->n, boundary, &mp);
+  if (st != DCTF_OK) return st;
+  op->mh = mh; op->mw = mw; op->ar = anchor[0]; op->ac = anchor[1];
+  op->boundary = boundary;
+  op->f16_scale_exp = f16_scale_exponent(mp);
+  cudaError_t e = launch_build(op, mp, stream);
+  if (e != cudaSuccess) return cuda_error(e, "operator build launch");
+  return DCTF_OK;
+}
+
+dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p) {
+  if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
+  if (p == DCTF_FP32_SIMT) { op->precision = p; return DCTF_OK; }
+  if (p < DCTF_FP32_SIMT || p > DCTF_TF32X3)
+    return set_error(DCTF_EINVAL, "unknown precision %d", (int)p);
+  if (!tc_supported(op->n, p))
+    return set_error(DCTF_EUNSUPPORTED, "precision %d has no kernel for n=%d", (int)p, op->n);
+  op->precision = p;
+  return DCTF_OK;
+}
+
+dctf_status dctf_operator_download(const dctf_operator *op, double *M_host, double *H_host) {
+  if (op == nullptr || M_host == nullptr) return set_error(DCTF_EINVAL, "NULL argument");
+  size_t bytes = (size_t)op->n2 * op->n2 * sizeof(double);
+  DCTF_CUDA(cudaDeviceSynchronize());
+  DCTF_CUDA(cudaMemcpy(M_host, op->d_M64, bytes, cudaMemcpyDeviceToHost));
+  if (H_host) DCTF_CUDA(cudaMemcpy(H_host, op->d_H64, bytes, cudaMemcpyDeviceToHost));
+  return DCTF_OK;
+}
+
+dctf_status dctf_operator_status(dctf_operator *op, uint32_t *code, int clear) {
+  if (op == nullptr || code == nullptr) return set_error(DCTF_EINVAL, "NULL argument");
+  DCTF_CUDA(cudaDeviceSynchronize());
+  DCTF_CUDA(cudaMemcpy(code, op->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (clear) {
+    DCTF_CUDA(cudaMemset(op->d_err, 0, sizeof(uint32_t)));
+    DCTF_CUDA(cudaDeviceSynchronize());
+  }
+  return DCTF_OK;
+}
+
+void dctf_release_operator(dctf_operator *op) {
+  if (op == nullptr) return;
+  for (int i = 0; i < 2; ++i) {
+    if (op->host_streams[i]) cudaStreamDestroy(op->host_streams[i]);
+    if (op->host_events[i]) cudaEventDestroy(op->host_events[i]);
+    for (int j = 0; j < 2; ++j)
+      if (op->d_stage[i][j]) cudaFree(op->d_stage[i][j]);
+  }
+  if (op->d_base) cudaFree(op->d_base);
+  delete op;
+}
+
+static dctf_status check_apply(const dctf_operator *op, const void *in, size_t in_elem,
+                               int64_t nblocks, const float *out) {
+  if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
+  if (nblocks < 0) return set_error(DCTF_EINVAL, "nblocks=%lld < 0", (long long)nblocks);
+  if (nblocks == 0) return DCTF_OK;
+  if (in == nullptr || out == nullptr) return set_error(DCTF_EINVAL, "coefficient pointer is NULL");
+  if (!aligned16(in) || !aligned16(out))
+    return set_error(DCTF_EINVAL, "coefficient pointers must be 16-byte aligned");
+  if (nblocks > (int64_t)1 << 31) return set_error(DCTF_EINVAL, "nblocks too large");
+  const char *a = static_cast<const char *>(in);
+  const char *b = reinterpret_cast<const char *>(out);
+  size_t la = (size_t)nblocks * op->n2 * in_elem, lb = (size_t)nblocks * op->n2 * sizeof(float);
+  if (a != b && a < b + lb && b < a + la)
+    return set_error(DCTF_EINVAL, "input and output overlap without being equal");
+  return DCTF_OK;
+}
+
+dctf_status dctf_apply(const dctf_operator *op, const float *coeffs, int64_t nblocks,
+                       float *out, dctf_stream_t stream) {
+  dctf_status st = check_apply(op, coeffs, sizeof(float), nblocks, out);
+  if (st != DCTF_OK || nblocks == 0) return st;
+  cudaError_t e;
+  if (op->precision == DCTF_FP32_SIMT)
+    e = launch_apply_simt(op, coeffs, nullptr, nblocks, out, stream);
+  else
+    e = launch_apply_tc(op, coeffs, nblocks, out, stream);
+  if (e != cudaSuccess) return cuda_error(e, "dctf_apply launch");
+  return DCTF_OK;
+}
+
+dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs, int64_t nblocks,
+                             float *out, dctf_stream_t stream) {
+  dctf_status st = check_apply(op, coeffs, sizeof(double), nblocks, out);
+  if (st != DCTF_OK || nblocks == 0) return st;
+  if (static_cast<const void *>(coeffs) == static_cast<const void *>(out))
+    return set_error(DCTF_EINVAL, "FP64 input cannot be filtered in place into FP32");
+  cudaError_t e = launch_apply_simt(op, nullptr, coeffs, nblocks, out, stream);
+  if (e != cudaSuccess) return cuda_error(e, "dctf_apply_f64in launch");
+  return DCTF_OK;
+}
+
+dctf_status dctf_apply_host(dctf_operator *op, const float *host_in, int64_t nblocks,
+                            float *host_out) {
+  if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
+  if (nblocks < 0) return set_error(DCTF_EINVAL, "nblocks < 0");
+  if (nblocks == 0) return DCTF_OK;
+  if (host_in == nullptr || host_out == nullptr) return set_error(DCTF_EINVAL, "NULL buffer");
+  const int64_t chunk = 65536;
+  const size_t row = (size_t)op->n2 * sizeof(float);
+  if (op->d_stage[0][0] == nullptr) {
+    for (int i = 0; i < 2; ++i) {
+      for (int j = 0; j < 2; ++j) DCTF_CUDA(cudaMalloc(&op->d_stage[i][j], chunk * row));
+      DCTF_CUDA(cudaStreamCreateWithFlags(&op->host_streams[i], cudaStreamDefault));
+      DCTF_CUDA(cudaEventCreateWithFlags(&op->host_events[i], cudaEventDisableTiming));
+    }
+    op->stage_blocks = chunk;
+  }
+  // chunk c uses stream / buffers c % 2: its H2D overlaps chunk c-1's
+  // compute and D2H (separate copy engines per direction).
+  int64_t nchunks = (nblocks + chunk - 1) / chunk;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    int k = (int)(c & 1);
+    int64_t b0 = c * chunk, nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
+    cudaStream_t s = op->host_streams[k];
+    DCTF_CUDA(cudaMemcpyAsync(op->d_stage[k][0], host_in + b0 * op->n2, nb * row,
+                              cudaMemcpyHostToDevice, s));
+    dctf_status st = dctf_apply(op, op->d_stage[k][0], nb, op->d_stage[k][1], s);
+    if (st != DCTF_OK) return st;
+    DCTF_CUDA(cudaMemcpyAsync(host_out + b0 * op->n2, op->d_stage[k][1], nb * row,
+                              cudaMemcpyDeviceToHost, s));
+  }
+  for (int k = 0; k < 2; ++k) DCTF_CUDA(cudaStreamSynchronize(op->host_streams[k]));
+  return DCTF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>              // CUtensorMap (type only; the driver entry is
+                               // fetched at run time, libcuda is not linked)
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "dctf.h"
+
+namespace dctf {
+
+// ------------------------------------------------------------ host errors
+dctf_status set_error(dctf_status s, const char *fmt, ...);
+dctf_status cuda_error(cudaError_t e, const char *what);
+
+#define DCTF_CUDA(call)                                                     \
+  do {                                                                      \
+    cudaError_t e__ = (call);                                               \
+    if (e__ != cudaSuccess) return ::dctf::cuda_error(e__, #call);          \
+  } while (0)
+
+// Largest mask the build kernels take (parameters travel by value).
+constexpr int kMaxN = 16;
+constexpr int kMaxN2 = kMaxN * kMaxN;
+
+struct MaskParams {
+  double w[kMaxN * kMaxN];   // row-major mh x mw
+  int mh, mw, ar, ac, n, boundary;
+};
+
+// Byte layout of the tensor-core B operand ("pieces"): for every 64-element
+// chunk kc of the input index k, R stacked rows of 128 bytes (64 fp16/bf16,
+// or 32 fp32), 16-byte units XOR-swizzled by (row & 7), i.e. the canonical
+// K-major SWIZZLE_128B layout, so a linear copy into 1024-aligned shared
+// memory is directly usable by tcgen05.mma.
+__host__ __device__ inline size_t sw128_offset(int row, int byte_in_row,
+                                               int rows, int chunk) {
+  int unit = byte_in_row >> 4;
+  return ((size_t)chunk * rows + row) * 128 + (size_t)(((unit ^ (row & 7)) << 4) | (byte_in_row & 15));
+}
+
+}  // namespace dctf
+
+// The opaque operator handle.
+struct dctf_operator {
+  int device;
+  int n, n2;
+  int mh, mw, ar, ac;
+  int boundary;
+  dctf_precision precision;
+  int f16_scale_exp;        // pieces hold M * 2^f16_scale_exp
+  // one device allocation, carved:
+  void *d_base;
+  size_t bytes;
+  double *d_M64;            // [n2][n2] FP64 operator, row = output coefficient
+  double *d_H64;            // [n2][n2] spatial operator
+  double *d_G64;            // [n2][n2] scratch: H K^T
+  float *d_M32;             // [n2][n2] FP32 copy of M
+  float *d_Mdc;             // [n2] M[:, 0] in FP32
+  __half *d_f16;            // F16X3 pieces: rows 0..n2-1 hi, n2..2n2-1 lo (sw128)
+  uint32_t *d_err;          // device status word
+  // dctf_apply_host staging (lazily allocated)
+  float *d_stage[2][2];
+  size_t stage_blocks;
+  cudaStream_t host_streams[2];
+  cudaEvent_t host_events[2];
+};
+
+namespace dctf {
+
+// builder.cu
+cudaError_t launch_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s);
+
+// apply_simt.cu
+cudaError_t launch_apply_simt(const dctf_operator *op, const float *x,
+                              const double *x64, int64_t nblocks, float *y,
+                              cudaStream_t s);
+
+// apply_tc.cu
+bool tc_supported(int n, dctf_precision p);
+cudaError_t launch_apply_tc(const dctf_operator *op, const float *x,
+                            int64_t nblocks, float *y, cudaStream_t s);
+
+int sm_count(int device);
+
+}  // namespace dctf

@@ -1,0 +1,220 @@
+"""GPU: y_b = M x_b through the C ABI against the FP64 oracle.
+
+Bars (stated once, used everywhere):
+  * coefficients: max |y_gpu - y_oracle| <= 1e-3 (0-255 pixel scale), the
+    oracle applied to the same FP32 input coefficients;
+  * pixels: uint8 of the GPU result (inverse DCT, round half away, saturate)
+    equals uint8 of the oracle's spatial-domain filter for every pixel whose
+    FP64 value is not within 1e-4 of a .5 rounding boundary (those are counted).
+"""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+COEF_TOL = 1e-3
+BAND = 1e-4
+
+
+def coeffs_of(img, n):
+    blocks = oracle.image_to_blocks(img, n)
+    return blocks, oracle.dct2_blocks(blocks)
+
+
+def run(dctf, op, x32, prec, inplace=False):
+    op.set_precision(prec)
+    xd = torch.from_numpy(np.ascontiguousarray(x32)).cuda()
+    yd = xd if inplace else torch.empty_like(xd)
+    dctf.apply(op, xd, x32.shape[0], yd)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy().astype(np.float64)
+
+
+def check(y, x32, blocks, w, a, n, boundary, pixels=True):
+    y_ref = oracle.apply_M(oracle.build_M(w, a, n, boundary), x32.astype(np.float64))
+    err = np.abs(y - y_ref).max()
+    assert err <= COEF_TOL, f"max coefficient error {err}"
+    if pixels:
+        p_sp = oracle.spatial_filter_blocks(blocks, w, a, boundary)
+        st = oracle.uint8_compare(p_sp, oracle.to_uint8(oracle.idct2_blocks(y, n)), BAND)
+        assert st["mismatch"] == 0, st
+    return err
+
+
+def precisions(n, dctf):
+    return [dctf.FP32_SIMT, dctf.F16X3] if n == 8 else [dctf.FP32_SIMT]
+
+
+@pytest.fixture(scope="module")
+def ragged_source():
+    img = datagen.synthetic_image(2048, 1280, datagen.rng(90, 0, 0))
+    blocks, x = coeffs_of(img, 8)
+    return blocks, x.astype(np.float32)
+
+
+@pytest.mark.parametrize("nb", [1, 5, 127, 128, 129, 255, 1000, 16384 + 77, 40960])
+@pytest.mark.parametrize("prec", ["simt", "f16x3"])
+def test_ragged_block_counts(dctf, ragged_source, nb, prec):
+    blocks, x = ragged_source
+    w, a = datagen.headline_mask(), (1, 3)
+    op = dctf.build_operator(w, a, 8, dctf.REPLICATE)
+    p = dctf.FP32_SIMT if prec == "simt" else dctf.F16X3
+    y = run(dctf, op, x[:nb], p)
+    check(y, x[:nb], blocks[:nb], w, a, 8, oracle.REPLICATE)
+    assert op.status() == 0
+
+
+def test_small_workload_fp64_coefficients(dctf):
+    """256x256, 3x3 Gaussian sigma=1, zero padding, FP64 coefficients in."""
+    job = datagen.small_job()
+    blocks, x64 = coeffs_of(job.image, 8)
+    op = dctf.build_operator(job.mask, job.anchor, 8, job.boundary)
+    xd = torch.from_numpy(x64).cuda()
+    yd = torch.empty(x64.shape, dtype=torch.float32, device="cuda")
+    dctf.apply_f64in(op, xd, x64.shape[0], yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy().astype(np.float64)
+    y_ref = oracle.apply_M(oracle.build_M(job.mask, job.anchor, 8, job.boundary), x64)
+    assert np.abs(y - y_ref).max() <= COEF_TOL
+    p_sp = oracle.spatial_filter_blocks(blocks, job.mask, job.anchor, job.boundary)
+    assert oracle.uint8_compare(p_sp, oracle.to_uint8(oracle.idct2_blocks(y, 8)))["mismatch"] == 0
+    for p in precisions(8, dctf):
+        check(run(dctf, op, x64.astype(np.float32), p), x64.astype(np.float32), blocks,
+              job.mask, job.anchor, 8, job.boundary)
+
+
+@pytest.mark.parametrize("prec", ["simt", "f16x3"])
+def test_headline_mask_1024(dctf, prec):
+    job = datagen.headline_job(1024, 1024)
+    blocks, x = coeffs_of(job.image, 8)
+    x = x.astype(np.float32)
+    op = dctf.build_operator(job.mask, job.anchor, 8, job.boundary)
+    p = dctf.FP32_SIMT if prec == "simt" else dctf.F16X3
+    check(run(dctf, op, x, p), x, blocks, job.mask, job.anchor, 8, job.boundary)
+
+
+@pytest.mark.parametrize("i", range(8))
+def test_grouped_masks(dctf, i):
+    """The four masks of the grouped batch with both boundary modes."""
+    w, a, boundary, _ = datagen.grouped_mask(i)
+    img = datagen.synthetic_image(256, 384, datagen.rng(91, i, 0))
+    blocks, x = coeffs_of(img, 8)
+    x = x.astype(np.float32)
+    op = dctf.build_operator(w, a, 8, boundary)
+    for p in precisions(8, dctf):
+        check(run(dctf, op, x, p), x, blocks, w, a, 8, boundary)
+
+
+def test_magic_square_replicate(dctf):
+    """Second experiment of Sec. III: unnormalised order-3 magic square."""
+    img = datagen.synthetic_image(256, 256, datagen.rng(92, 0, 0))
+    blocks, x = coeffs_of(img, 8)
+    x = x.astype(np.float32)
+    w = datagen.magic_square_3()
+    op = dctf.build_operator(w, (1, 1), 8, dctf.REPLICATE)
+    for p in precisions(8, dctf):
+        y = run(dctf, op, x, p)
+        y_ref = oracle.apply_M(oracle.build_M(w, (1, 1), 8, oracle.REPLICATE), x.astype(np.float64))
+        # outputs reach 45 x 2040: the bar scales with the output magnitude
+        assert np.abs(y - y_ref).max() <= COEF_TOL * 45
+        p_sp = oracle.spatial_filter_blocks(blocks, w, (1, 1), oracle.REPLICATE)
+        st = oracle.uint8_compare(p_sp, oracle.to_uint8(oracle.idct2_blocks(y, 8)), BAND)
+        assert st["mismatch"] == 0
+
+
+@pytest.mark.parametrize("n", [4, 16])
+def test_other_block_sizes(dctf, n):
+    img = datagen.synthetic_image(256, 320, datagen.rng(93, n, 0))
+    blocks, x = coeffs_of(img, n)
+    x = x.astype(np.float32)
+    if n == 16:
+        w, a = datagen.large_mask(), (4, 4)
+    else:
+        w, a = datagen.uniform_random_mask(3, 4, datagen.rng(93, n, 1)), (2, 1)
+    for boundary in (oracle.ZERO, oracle.REPLICATE):
+        op = dctf.build_operator(w, a, n, boundary)
+        for p in precisions(n, dctf):
+            check(run(dctf, op, x, p), x, blocks, w, a, n, boundary)
+        with pytest.raises(dctf.DctfError):
+            op.set_precision(dctf.F16X3)
+
+
+@pytest.mark.parametrize("prec", ["simt", "f16x3"])
+def test_in_place(dctf, ragged_source, prec):
+    blocks, x = ragged_source
+    x = x[:3000]
+    w, a = datagen.headline_mask(), (1, 3)
+    op = dctf.build_operator(w, a, 8, dctf.REPLICATE)
+    p = dctf.FP32_SIMT if prec == "simt" else dctf.F16X3
+    y_sep = run(dctf, op, x, p)
+    y_inp = run(dctf, op, x, p, inplace=True)
+    assert np.array_equal(y_sep, y_inp)
+
+
+def test_zero_blocks_and_bad_pointers(dctf):
+    op = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 8, dctf.ZERO)
+    dctf.apply(op, 0, 0, 0)                       # nothing to do, nothing touched
+    buf = torch.zeros(2 * 64 + 4, device="cuda")
+    with pytest.raises(dctf.DctfError):
+        dctf.apply(op, buf.data_ptr() + 4, 2, buf.data_ptr() + 4 + 512)   # misaligned
+    with pytest.raises(dctf.DctfError):
+        dctf.apply(op, buf.data_ptr(), 2, buf.data_ptr() + 256)           # partial overlap
+    with pytest.raises(dctf.DctfError):
+        dctf.apply(op, buf.data_ptr(), -1, buf.data_ptr())
+
+
+def test_forward_and_inverse_dct(dctf):
+    img = datagen.synthetic_image(64, 96, datagen.rng(94, 0, 0))
+    for n in (4, 8, 16):
+        blocks, x_ref = coeffs_of(img, n)
+        imd = torch.from_numpy(img).cuda()
+        c64 = torch.empty(x_ref.shape, dtype=torch.float64, device="cuda")
+        dctf.forward_dct(imd, 64, 96, n, c64, f64=True)
+        c32 = torch.empty(x_ref.shape, dtype=torch.float32, device="cuda")
+        dctf.forward_dct(imd, 64, 96, n, c32)
+        torch.cuda.synchronize()
+        assert np.abs(c64.cpu().numpy() - x_ref).max() < 1e-10
+        assert np.abs(c32.cpu().numpy() - x_ref).max() < 2e-4
+        back = torch.empty_like(imd)
+        dctf.inverse_dct_u8(c32, 64, 96, n, back)
+        torch.cuda.synchronize()
+        assert np.array_equal(back.cpu().numpy(), img)
+
+
+def test_apply_host_matches_device(dctf, ragged_source):
+    _, x = ragged_source
+    op = dctf.build_operator(datagen.headline_mask(), (1, 3), 8, dctf.REPLICATE)
+    y_dev = run(dctf, op, x, dctf.F16X3)
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    dctf.apply_host(op, hin, x.shape[0], hout)
+    assert np.array_equal(hout.numpy().astype(np.float64), y_dev)
+
+
+@pytest.fixture(scope="module")
+def headline_full():
+    job = datagen.headline_job()           # 4096 x 4096, 262,144 blocks
+    blocks, x = coeffs_of(job.image, 8)
+    return job, blocks, x.astype(np.float32)
+
+
+def test_full_size_headline_sampled(dctf, headline_full):
+    """The full 4096x4096 workload in the benchmark's launch configuration;
+    the oracle checks a sample of blocks (first and last tile, random rest),
+    and the two kernels agree on every block."""
+    job, blocks, x = headline_full
+    op = dctf.build_operator(job.mask, job.anchor, 8, job.boundary)
+    y_tc = run(dctf, op, x, dctf.F16X3)
+    y_simt = run(dctf, op, x, dctf.FP32_SIMT)
+    nb = x.shape[0]
+    g = np.random.default_rng(95)
+    idx = np.unique(np.concatenate([np.arange(128), np.arange(nb - 128, nb),
+                                    g.integers(0, nb, 4096)]))
+    for y in (y_tc, y_simt):
+        check(y[idx], x[idx], blocks[idx], job.mask, job.anchor, 8, job.boundary)
+    assert np.abs(y_tc - y_simt).max() <= 2 * COEF_TOL
+    assert op.status() == 0
