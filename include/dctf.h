@@ -163,6 +163,26 @@ dctf_status dctf_inverse_dct_u8(const float *coeffs, int height, int width,
                                 int n, uint8_t *image, int64_t pitch,
                                 dctf_stream_t stream);
 
+/* Build the FP64 operator M (and optionally H) for one mask into memory the
+ * caller provides, allocating nothing.  The paper has no counterpart: this
+ * exists for callers that cannot call cudaMalloc -- code inside a framework
+ * whose pool owns all device memory, real-time paths where cudaMalloc's
+ * implicit device synchronisation is not allowed, plug-ins that are handed
+ * only the buffers they read and write.
+ *  M_out  device, n2*n2 doubles (row = output coefficient), 16-byte aligned.
+ *  H_out  device, n2*n2 doubles, or NULL.
+ * Same arguments and checks as dctf_build_operator otherwise; asynchronous
+ * on `stream`.  The build's scratch is a static 1 MiB device array inside the
+ * library (enough for the largest block, n = 16); sizes beyond it are
+ * rejected with DCTF_EINVAL.  The first call on a device looks up that
+ * array's device address, so make it before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller. */
+dctf_status dctf_build_matrix_noalloc(const double *mask, int mh, int mw,
+                                      const int anchor[2], int n,
+                                      dctf_boundary boundary, double *M_out,
+                                      double *H_out, dctf_stream_t stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *dctf_last_error(void);
 

@@ -44,6 +44,7 @@ _SIGS = {
     "dctf_forward_dct": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
     "dctf_forward_dct_f64": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
     "dctf_inverse_dct_u8": (_i32, [_vp, _i32, _i32, _i32, _vp, _i64, _vp]),
+    "dctf_build_matrix_noalloc": (_i32, [_vp, _i32, _i32, _vp, _i32, _i32, _vp, _vp, _vp]),
     "dctf_last_error": (ctypes.c_char_p, []),
     "dctf_version": (_i32, []),
 }

@@ -12,6 +12,10 @@
 //   build_hg: row p of H (a1) and row p of G = H K^T (first half of a2);
 //   build_m : column q of M = K G (second half of a2), its FP32 copy and the
 //             FP16 hi/lo pieces (a3), written in the tensor-core B layout.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
 #include "dctf_internal.cuh"
 
 namespace dctf {
@@ -119,3 +123,132 @@ cudaError_t launch_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s
 }
 
 }  // namespace dctf
+
+// ---------------------------------------------------------------------------
+// Allocation-free build of M into caller memory.
+//
+// For callers that may not allocate device memory: code running inside a
+// framework that owns every byte of the GPU through its own pool, real-time
+// paths where cudaMalloc's implicit device synchronisation is not allowed,
+// or plug-ins handed only the buffers they read and write.  The build's one
+// scratch buffer (G = H K^T, and H when the caller does not want it) lives in
+// this file-scope array instead of an allocation.  It is 1 MiB, sized for the
+// largest block (n = 16: two 256 x 256 FP64 matrices), and every GPU that
+// loads the library holds it until the process exits.
+static __device__ __align__(256) double dctf_build_scratch[2 * dctf::kMaxN2 * dctf::kMaxN2];
+
+namespace dctf {
+namespace {
+
+constexpr size_t kScratchDoubles = 2 * (size_t)kMaxN2 * kMaxN2;
+
+// Same arithmetic as build_hg_kernel; H is optional here.
+__global__ void build_hg_noalloc_kernel(const MaskParams mp, double *__restrict__ H,
+                                        double *__restrict__ G) {
+  __shared__ double cs[kMaxN][kMaxN + 1];
+  __shared__ double hrow[kMaxN2];
+  __shared__ double tmp[kMaxN2];
+  const int n = mp.n, n2 = n * n, p = blockIdx.x, t = threadIdx.x;
+  const int i = p / n, j = p % n;
+  dct_matrix_smem(cs, n);
+  if (t < n2) hrow[t] = 0.0;
+  __syncthreads();
+  if (t == 0) {
+    for (int r = 0; r < mp.mh; ++r)
+      for (int c = 0; c < mp.mw; ++c) {
+        int s = i + r - mp.ar, u = j + c - mp.ac;
+        if (mp.boundary == DCTF_ZERO) {
+          if (s < 0 || s >= n || u < 0 || u >= n) continue;
+        } else {
+          s = min(max(s, 0), n - 1);
+          u = min(max(u, 0), n - 1);
+        }
+        hrow[s * n + u] += mp.w[r * mp.mw + c];
+      }
+  }
+  __syncthreads();
+  if (t < n2 && H != nullptr) H[(size_t)p * n2 + t] = hrow[t];
+  double g = dct2_vec(hrow, tmp, cs, n, t);
+  if (t < n2) G[(size_t)p * n2 + t] = g;
+}
+
+// Same arithmetic as build_m_kernel; writes M (FP64) only.
+__global__ void build_m_noalloc_kernel(int n, const double *__restrict__ G,
+                                       double *__restrict__ M64) {
+  __shared__ double cs[kMaxN][kMaxN + 1];
+  __shared__ double gcol[kMaxN2];
+  __shared__ double tmp[kMaxN2];
+  const int n2 = n * n, q = blockIdx.x, t = threadIdx.x;
+  dct_matrix_smem(cs, n);
+  if (t < n2) gcol[t] = G[(size_t)t * n2 + q];
+  __syncthreads();
+  double m = dct2_vec(gcol, tmp, cs, n, t);
+  if (t < n2) M64[(size_t)t * n2 + q] = m;
+}
+
+std::mutex g_scratch_mu;
+double *g_scratch_addr[64];
+
+// Device address of the static scratch on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device pointer).
+cudaError_t scratch_on_current_device(double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_addr[dev] == nullptr) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, dctf_build_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace dctf
+
+extern "C" dctf_status dctf_build_matrix_noalloc(const double *mask, int mh, int mw,
+                                                 const int anchor[2], int n,
+                                                 dctf_boundary boundary, double *M_out,
+                                                 double *H_out, dctf_stream_t stream) {
+  using namespace dctf;
+  if (n != 4 && n != 8 && n != 16)
+    return set_error(DCTF_EINVAL, "block size n=%d: must be 4, 8 or 16", n);
+  const size_t n2 = (size_t)n * n;
+  if (2 * n2 * n2 > kScratchDoubles)
+    return set_error(DCTF_EINVAL, "n=%d needs %zu scratch doubles; the static scratch holds %zu",
+                     n, 2 * n2 * n2, kScratchDoubles);
+  if (mask == nullptr || anchor == nullptr || M_out == nullptr)
+    return set_error(DCTF_EINVAL, "mask, anchor and M_out must not be NULL");
+  if ((reinterpret_cast<uintptr_t>(M_out) & 15) || (reinterpret_cast<uintptr_t>(H_out) & 15))
+    return set_error(DCTF_EINVAL, "M_out and H_out must be 16-byte aligned");
+  if (mh < 1 || mw < 1 || mh > n || mw > n)
+    return set_error(DCTF_EINVAL, "mask %dx%d must fit in the %dx%d block", mh, mw, n, n);
+  if (anchor[0] < 0 || anchor[0] >= mh || anchor[1] < 0 || anchor[1] >= mw)
+    return set_error(DCTF_EINVAL, "anchor (%d,%d) outside the %dx%d mask", anchor[0], anchor[1],
+                     mh, mw);
+  if (boundary != DCTF_ZERO && boundary != DCTF_REPLICATE)
+    return set_error(DCTF_EINVAL, "boundary %d: must be DCTF_ZERO or DCTF_REPLICATE", boundary);
+  MaskParams mp;
+  memset(&mp, 0, sizeof mp);
+  for (int k = 0; k < mh * mw; ++k) {
+    if (!isfinite(mask[k])) return set_error(DCTF_EINVAL, "mask entry %d is not finite", k);
+    mp.w[k] = mask[k];
+  }
+  mp.mh = mh; mp.mw = mw; mp.ar = anchor[0]; mp.ac = anchor[1]; mp.n = n; mp.boundary = boundary;
+  double *scratch = nullptr;
+  cudaError_t e = scratch_on_current_device(&scratch);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static build scratch)");
+  double *G = scratch;                                  // first half
+  double *H = H_out != nullptr ? H_out : scratch + n2 * n2;
+  build_hg_noalloc_kernel<<<(unsigned)n2, (unsigned)n2, 0, stream>>>(mp, H, G);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "no-alloc build launch");
+  build_m_noalloc_kernel<<<(unsigned)n2, (unsigned)n2, 0, stream>>>(n, G, M_out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "no-alloc build launch");
+  return DCTF_OK;
+}
