@@ -274,6 +274,14 @@ def run_dctf(args):
         simt = {"value": ws * nb * args.steps / (s_total / 1e3), "ms_per_step": s_total / args.steps,
                 "apply_us": 1e3 * s_mean,
                 "apply_GBps": BYTES_PER_BLOCK * nb / (s_mean / 1e3) / 1e9}
+    # the operator build alone (2 kernels, one graph replay), for the record
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(100):
+        g_build.replay()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    build_us = 10.0 * b0.elapsed_time(b1)
     time.sleep(0.2)
     sampler.stop()
     clocks = sampler.summary(t0, t1)
@@ -307,6 +315,7 @@ def run_dctf(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "blocks_per_step": nb, "precision": "F16X3",
                    "step": "operator rebuild (FP64, 2 kernels) + apply (1 kernel)",
+                   "build_us": build_us,
                    "l2": f"{ROTATE} rotating input/output buffer pairs, "
                          f"{ROTATE * 2 * nb * 256 / 1e9:.2f} GB > L2",
                    "parallelism": f"dp{ws} (independent images, no collective)"},
