@@ -4,10 +4,12 @@
 One step = one pass of the whole path over one image: rebuild the operator
 on the device in FP64 for the step's mask (H, M = K H K^T, FP16 pieces) and
 apply it to all 262,144 8x8 blocks (FP32 coefficients in HBM -> filtered
-FP32 coefficients in HBM).  Each step runs as two CUDA-graph replays (build,
-apply) on one stream, with CUDA events around the apply to time that kernel
-live.  Inputs rotate over 8 buffer pairs (1.07 GB > 129 MB of L2), so no step
-reads its input from L2.
+FP32 coefficients in HBM).  The timed loop is one CUDA graph: the apply of
+step i runs on the main branch with operator i % 2 while a side branch
+rebuilds the other operator for step i + 1; CUDA events bracket the graph.
+The apply kernel is then timed alone the same way (K back-to-back applies
+in one graph, events at both ends) for its roofline.  Inputs rotate over 8
+buffer pairs (1.07 GB > 129 MB of L2), so no step reads its input from L2.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
 the host cores instead (bounded sample of the same workload).
@@ -40,7 +42,7 @@ ROTATE = 8
 
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
-NCU_TRAFFIC = {}               # {sha1 of apply_tc.cu: bytes per launch}
+NCU_TRAFFIC = {}               # {sha1 of apply_group.cu: bytes per launch}
 
 
 def parse():
@@ -53,6 +55,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=0, help="0: same as --steps, capped at 500")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-simt", action="store_true", help="skip the FP32 CUDA-core comparison")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving (p50/p99) phase")
+    p.add_argument("--serving-requests", type=int, default=400)
     return p.parse_args()
 
 
@@ -73,7 +77,7 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_1710_07193_gb300", "csrc", "apply_tc.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1710_07193_gb300", "csrc", "apply_group.cu"), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
@@ -183,11 +187,80 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving
+SERVING_RATES = (500.0, 1000.0, 2000.0)
+
+
+def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
+    """Poisson request stream through the continuous-batching server: half
+    1920x1088 4:2:0 frames (3 int16 planes), half 512x512 stills, each with
+    one of 32 seeded masks and per-plane quantisation tables.  Returns the
+    stats of every rate and the highest rate whose p99 stays under 10 ms."""
+    dev = torch.device("cuda")
+    # a pool of quantised planes, made on the device (forward DCT + quantise)
+    pool = {}
+    for kind, shapes in (("frame", datagen.FRAME_PLANES), ("still", datagen.STILL_PLANES)):
+        for v in range(2):
+            for p, (h, w) in enumerate(shapes):
+                img = torch.from_numpy(datagen.synthetic_image(
+                    h, w, datagen.rng(datagen.W_SERVING, 9000 + v, 10 + p))).to(dev)
+                for sc in (1, 2, 4):
+                    q = torch.from_numpy(datagen.quant_table(sc).ravel().astype(np.int16)).to(dev)
+                    out = torch.empty(((h // 8) * (w // 8), 64), dtype=torch.int16, device=dev)
+                    lib.forward_dct_i16(img, h, w, 8, q, out)
+                    pool[(kind, v, p, sc)] = out.cpu().numpy()
+    qtabs = {sc: datagen.quant_table(sc).ravel() for sc in (1, 2, 4)}
+    masks = [datagen.serving_mask(j) for j in range(32)]
+    results = []
+    for rate in rates:
+        stream = datagen.serving_stream(n_requests, rate, with_pixels=False)
+        srv = lib.Server(hbm_budget_bytes=1 << 30, max_inflight=3, max_batch_requests=16,
+                         op_cache_capacity=64)
+        ring = 48
+        outs = [None] * ring
+        tickets = []
+        t0 = time.perf_counter()
+        base = stream[0].arrival_s
+        for i, r in enumerate(stream):
+            if i >= ring:
+                srv.wait(tickets[i - ring])              # free the output ring entry
+            target = t0 + (r.arrival_s - base)
+            while time.perf_counter() < target:
+                pass
+            v = i % 2
+            ins = [pool[(r.kind, v, p, sc)] for p, sc in enumerate(r.q_scale)]
+            if outs[i % ring] is None or len(outs[i % ring]) != len(ins) or any(
+                    o.shape != x.shape for o, x in zip(outs[i % ring], ins)):
+                outs[i % ring] = [np.empty_like(x) for x in ins]
+            w, a, bnd = masks[r.mask_id]
+            tickets.append(srv.submit(ins, outs[i % ring], [qtabs[sc] for sc in r.q_scale],
+                                      w, a, bnd))
+        for t in tickets[max(0, len(tickets) - ring):]:
+            srv.wait(t)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        frames = sum(1 for r in stream if r.kind == "frame")
+        results.append({"rate_req_s": rate, "requests": n_requests, "p50_ms": st["p50_ms"],
+                        "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                        "frames_per_s": frames / wall, "requests_per_s": n_requests / wall,
+                        "blocks_per_s": st["blocks"] / wall, "batches": st["batches"],
+                        "max_batch": st["max_batch_requests_seen"],
+                        "cache_hit_rate": st["cache_hits"] / max(1, st["cache_hits"] + st["cache_misses"]),
+                        "failed": st["failed"]})
+    ok = [r for r in results if r["p99_ms"] < 10.0]
+    return {"stream": "Poisson; 50% 1920x1088 4:2:0 frames, 50% 512x512 stills; int16, "
+                      "q[u,v]=1+round(s(1+u+v)), s in {1,2,4}; 32 seeded masks 3x3..7x7",
+            "rates": results,
+            "headline": max(ok, key=lambda r: r["rate_req_s"]) if ok else None}
+
+
 # ------------------------------------------------------------------ our arm
 def run_dctf(args):
     import torch
     import torch.distributed as dist
     import paper_1710_07193_gb300 as lib
+    from paper_1710_07193_gb300 import shard
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -208,77 +281,103 @@ def run_dctf(args):
     xs = [x0.clone() for _ in range(ROTATE)]
     ys = [torch.empty_like(x0) for _ in range(ROTATE)]
     del img_d
-    op = lib.build_operator(job.mask, job.anchor, 8, job.boundary)
+    # two operators: step i applies ops[i % 2] while the side stream rebuilds
+    # the other one for step i + 1 (each step still builds its own operator)
+    ops = [lib.build_operator(job.mask, job.anchor, 8, job.boundary) for _ in range(2)]
     torch.cuda.synchronize()
 
-    def capture(fn):
+    def loop_graph(steps, prec):
+        """One CUDA graph of `steps` steps: build(i+1) on a side branch
+        overlapping apply(i) on the main branch."""
+        for op in ops:
+            op.set_precision(prec)
+        main, side = torch.cuda.Stream(), torch.cuda.Stream()
+        built = [torch.cuda.Event() for _ in range(steps)]
+        applied = [torch.cuda.Event() for _ in range(steps)]
+        # warm every call once outside capture (function attributes etc.)
+        with torch.cuda.stream(main):
+            ops[0].rebuild(job.mask, job.anchor, job.boundary)
+            lib.apply(ops[0], xs[0], nb, ys[0])
+        torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream()
-        s.wait_stream(stream)
-        with torch.cuda.stream(s):
-            fn()                                   # warm (attribute set-up) outside capture
-            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
-                fn()
-        stream.wait_stream(s)
+        with torch.cuda.graph(g, stream=main, capture_error_mode="thread_local"):
+            fork = torch.cuda.Event()
+            fork.record(main)
+            side.wait_event(fork)
+            with torch.cuda.stream(side):
+                ops[0].rebuild(job.mask, job.anchor, job.boundary)
+                built[0].record(side)
+            for i in range(steps):
+                main.wait_event(built[i])
+                lib.apply(ops[i % 2], xs[i % ROTATE], nb, ys[i % ROTATE], stream=main)
+                applied[i].record(main)
+                if i + 1 < steps:
+                    if i >= 1:
+                        side.wait_event(applied[i - 1])   # ops[(i+1)%2] last read by apply(i-1)
+                    with torch.cuda.stream(side):
+                        ops[(i + 1) % 2].rebuild(job.mask, job.anchor, job.boundary)
+                        built[i + 1].record(side)
+            join = torch.cuda.Event()
+            join.record(side)
+            main.wait_event(join)
         torch.cuda.synchronize()
         return g
 
-    g_build = capture(lambda: op.rebuild(job.mask, job.anchor, job.boundary))
+    def apply_graph(steps, prec):
+        """`steps` applies back to back (the dominant kernel alone)."""
+        ops[0].set_precision(prec)
+        main = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=main, capture_error_mode="thread_local"):
+            for i in range(steps):
+                lib.apply(ops[0], xs[i % ROTATE], nb, ys[i % ROTATE], stream=main)
+        torch.cuda.synchronize()
+        return g
 
-    def graphs_for(prec):
-        op.set_precision(prec)
-        return [capture(lambda j=j: lib.apply(op, xs[j], nb, ys[j])) for j in range(ROTATE)]
-
-    g_apply = graphs_for(lib.F16X3)
-    g_simt = None if args.no_simt else graphs_for(lib.FP32_SIMT)
-    op.set_precision(lib.F16X3)
-
-    def timed(graphs, steps, warmup, sampler=None):
-        for i in range(warmup):
-            g_build.replay()
-            graphs[i % ROTATE].replay()
+    def run_timed(g):
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-        ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
         t0 = time.time()
         start.record(stream)
-        for i in range(steps):
-            g_build.replay()
-            ev_a[i].record(stream)
-            graphs[i % ROTATE].replay()
-            ev_b[i].record(stream)
+        g.replay()
         end.record(stream)
         torch.cuda.synchronize()
         t1 = time.time()
         if ws > 1:
             dist.barrier()
-        total_ms = start.elapsed_time(end)
-        apply_ms = [a.elapsed_time(b) for a, b in zip(ev_a, ev_b)]
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), statistics.mean(apply_ms), statistics.median(apply_ms), (t0, t1)
+        return shard.max_over_ranks(start.elapsed_time(end), dist if ws > 1 else None), (t0, t1)
 
-    gpu_id = f"GPU-{torch.cuda.get_device_properties(dev).uuid}" if hasattr(
-        torch.cuda.get_device_properties(dev), "uuid") else str(local)
+    def timed(prec, steps, warmup):
+        g_w = loop_graph(max(warmup, 1), prec)
+        g_t = loop_graph(steps, prec)
+        g_w.replay()
+        total_ms, window = run_timed(g_t)
+        # the apply kernel alone, for its roofline: same launches, no builds
+        a_w, a_t = apply_graph(max(warmup, 1), prec), apply_graph(steps, prec)
+        a_w.replay()
+        apply_ms, _ = run_timed(a_t)
+        return total_ms, apply_ms / steps, window
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if hasattr(props, "uuid") else str(local)
     sampler = ClockSampler(gpu_id)
     time.sleep(0.3)
-    total_ms, apply_mean, apply_med, (t0, t1) = timed(g_apply, args.steps, args.warmup)
+    total_ms, apply_mean, (t0, t1) = timed(lib.F16X3, args.steps, args.warmup)
     simt = None
-    if g_simt is not None:
-        s_total, s_mean, s_med, _ = timed(g_simt, args.steps, args.warmup)
+    if not args.no_simt:
+        s_total, s_mean, _ = timed(lib.FP32_SIMT, args.steps, args.warmup)
         simt = {"value": ws * nb * args.steps / (s_total / 1e3), "ms_per_step": s_total / args.steps,
                 "apply_us": 1e3 * s_mean,
                 "apply_GBps": BYTES_PER_BLOCK * nb / (s_mean / 1e3) / 1e9}
-    # the operator build alone (2 kernels, one graph replay), for the record
+    op = ops[0]
+    op.set_precision(lib.F16X3)
+    # the operator build alone (2 kernels), for the record
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     b0.record(stream)
     for _ in range(100):
-        g_build.replay()
+        op.rebuild(job.mask, job.anchor, job.boundary)
     b1.record(stream)
     torch.cuda.synchronize()
     build_us = 10.0 * b0.elapsed_time(b1)
@@ -303,7 +402,11 @@ def run_dctf(args):
            "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
            "steps": e2e_steps, "path": "dctf_apply_host, pinned host buffers, 64k-block chunks on 2 streams"}
 
-    status = op.status()
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(lib, torch, args.serving_requests)
+
+    status = ops[0].status() | ops[1].status()
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_BLOCK * nb / (apply_mean / 1e3) / 1e9
     traffic = NCU_TRAFFIC.get(kernel_source_hash())
@@ -314,7 +417,9 @@ def run_dctf(args):
         "vs_baseline": None, "dtype": "f32 (f16x3 tensor-core split, fp32 accumulate)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "blocks_per_step": nb, "precision": "F16X3",
-                   "step": "operator rebuild (FP64, 2 kernels) + apply (1 kernel)",
+                   "step": "operator rebuild (FP64, 2 kernels) + apply (1 kernel); "
+                           "build of step i+1 overlaps apply of step i (two operators)",
+                   "submission": "one CUDA graph per timed loop",
                    "build_us": build_us,
                    "l2": f"{ROTATE} rotating input/output buffer pairs, "
                          f"{ROTATE * 2 * nb * 256 / 1e9:.2f} GB > L2",
@@ -322,10 +427,12 @@ def run_dctf(args):
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "apply_tc_f16x3_n8", "apply_us_mean": 1e3 * apply_mean,
-                     "apply_us_median": 1e3 * apply_med},
+                     "kernel": "apply_group_kernel<float,4,1,false> (one item)",
+                     "apply_us_mean": 1e3 * apply_mean,
+                     "timing": "events around K back-to-back applies in one CUDA graph"},
         "fp32_simt": simt,
         "e2e": e2e,
+        "serving": serving,
         "clocks": clocks,
         "device_status": status,
     }
@@ -337,7 +444,8 @@ def run_dctf(args):
                                           f"262144 blocks), {dt:.1f} s, numpy FP64"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    op.release()
+    for o in ops:
+        o.release()
     if ws > 1:
         dist.destroy_process_group()
 

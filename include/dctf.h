@@ -144,6 +144,123 @@ dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs,
 dctf_status dctf_apply_host(dctf_operator *op, const float *host_in,
                             int64_t nblocks, float *host_out);
 
+/* ---------------------------------------------------------------------
+ * Grouped apply: many images, each with its own operator, in ONE persistent
+ * launch (the same y_b = M x_b of Eq. 11 / Eq. 20 for every block of every
+ * item; 8x8 blocks, F16X3 tensor-core arithmetic).  All blocks of all items
+ * are split evenly over the persistent CTAs; each CTA switches operators at
+ * item boundaries without stalling (operator slots are loaded one segment
+ * ahead).
+ *
+ * DCTF_IO_I16 items hold JPEG-style quantised coefficients: the kernel
+ * dequantises x[k] = in[k] * q_in[k] on load and requantises
+ * out[k] = sat_int16(round_half_away(y[k] / q_out[k])) on store, so int16
+ * data goes from HBM to HBM in one pass. */
+typedef enum { DCTF_IO_F32 = 0, DCTF_IO_I16 = 1 } dctf_io;
+
+typedef struct {
+    const dctf_operator *op;  /* n = 8 operator (kept alive by the caller)     */
+    const void *in;           /* device [nblocks][64] float, or int16 for I16  */
+    void *out;                /* same shape and type; == in allowed, no other  */
+                              /* overlap                                       */
+    int64_t nblocks;          /* >= 0; 0 makes the item a no-op                */
+    const uint16_t *q_in;     /* device [64] quantisation table (I16), or NULL */
+    const uint16_t *q_out;    /* device [64] output table (I16), or NULL       */
+} dctf_group_item;
+
+typedef struct dctf_group dctf_group;
+
+/* Encode every item's TMA descriptors and upload them (synchronous, allocates
+ * device memory).  The items' buffers and operators must stay valid while the
+ * group is used.  Launch parameters start from the autotuner's cached choice
+ * for this size class, else one CTA per SM and 128-row tiles. */
+dctf_status dctf_group_create(const dctf_group_item *items, int nitems,
+                              dctf_io io, dctf_group **out);
+
+/* One persistent launch over every item, asynchronous on `stream`; no host
+ * work, so it can be captured in a CUDA graph and replayed. */
+dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream);
+
+/* Autotuner: time each candidate (CTA count x tile height) `reps` times on
+ * this group (it really runs the group: no item may be in place; EINVAL
+ * otherwise), keep the fastest for this group and cache it for its size
+ * class.  Synchronises `stream`. */
+dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps);
+
+/* The launch parameters in use: CTA count and tile height (64 or 128). */
+dctf_status dctf_group_config(const dctf_group *g, int *grid, int *tile_rows);
+
+/* Device status word of the group's launches (as dctf_operator_status). */
+dctf_status dctf_group_status(dctf_group *g, uint32_t *code, int clear);
+
+void dctf_group_destroy(dctf_group *g);
+
+/* One-shot form: create, launch on `stream`, wait for it, destroy.  Not for
+ * stream capture (it synchronises). */
+dctf_status dctf_apply_grouped(const dctf_group_item *items, int nitems,
+                               dctf_io io, dctf_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Serving: a continuous-batching request loop for JPEG-style quantised
+ * planes (the library's serving form of the per-block filter; the paper has
+ * no serving system).  A request carries 1-4 int16 planes [nblocks][64] with
+ * one quantisation table each (used to dequantise the input and requantise
+ * the output) and one 8x8-block mask.  A worker thread admits waiting
+ * requests in arrival order while a batch slot is free and their device
+ * memory fits in the HBM budget, reuses or builds their operators (device
+ * cache keyed by mask, anchor and boundary; FP64 build), and runs each batch
+ * as one grouped launch with dequantise / requantise fused; up to
+ * max_inflight batches overlap on the device.  Results do not depend on the
+ * batch a request lands in. */
+typedef struct {
+    size_t hbm_budget_bytes;        /* device arena for request planes (>= 1 MiB) */
+    int max_inflight;               /* batches in flight at once (1..8)           */
+    int max_batch_requests;         /* requests per batch (>= 1)                  */
+    int op_cache_capacity;          /* cached operators (>= 1)                    */
+    int inject_build_failure_every; /* test hook: fail every k-th build (0 off)   */
+} dctf_server_cfg;
+
+typedef struct {
+    int nplanes;                    /* 1..4                                        */
+    const int16_t *in[4];           /* host [nblocks][64], read during the call... */
+    int16_t *out[4];                /* ...and written before wait returns          */
+    int64_t nblocks[4];             /* > 0                                         */
+    const uint16_t *q[4];           /* host [64] quantisation table per plane      */
+    const double *mask;             /* host row-major mh x mw, copied at submit    */
+    int mh, mw;                     /* 1..8                                        */
+    int anchor[2];
+    dctf_boundary boundary;
+} dctf_request;
+
+typedef struct {
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> result in host buffer */
+    double wall_s;                           /* first submit -> last completion */
+    uint64_t completed, failed, batches, blocks, cache_hits, cache_misses;
+    int max_batch_requests_seen;
+    size_t hbm_in_use;
+} dctf_stats;
+
+typedef struct dctf_server dctf_server;
+
+/* Allocate the HBM arena, pinned staging of the same size and the batch
+ * slots on the current device; start the worker thread. */
+dctf_status dctf_server_create(const dctf_server_cfg *cfg, dctf_server **out);
+
+/* Queue a request; its host buffers must stay valid until dctf_server_wait
+ * returns for its ticket.  EBUDGET if it can never fit the HBM budget. */
+dctf_status dctf_server_submit(dctf_server *s, const dctf_request *req,
+                               uint64_t *ticket);
+
+/* Wait up to timeout_ms for a request: DCTF_OK once its outputs are written,
+ * ETIMEOUT if still running (the ticket stays valid), or the request's own
+ * error (the server keeps running).  A finished ticket is then retired. */
+dctf_status dctf_server_wait(dctf_server *s, uint64_t ticket, int timeout_ms);
+
+dctf_status dctf_server_stats(dctf_server *s, dctf_stats *out);
+
+/* Finish every queued and running request, then free everything. */
+void dctf_server_destroy(dctf_server *s);
+
 /* Blockwise forward DCT of a uint8 image (Sec. II.A, Eq. 1): block (by, bx)
  * in raster order b = by*(width/n) + bx gets BLOCK = C block C^T, written as
  * coeffs[b][u*n + v].  image: device, height x width bytes, row pitch `pitch`
@@ -155,6 +272,13 @@ dctf_status dctf_forward_dct(const uint8_t *image, int height, int width,
 dctf_status dctf_forward_dct_f64(const uint8_t *image, int height, int width,
                                  int64_t pitch, int n, double *coeffs,
                                  dctf_stream_t stream);
+
+/* Forward DCT followed by JPEG-style quantisation with a per-coefficient
+ * table q (device, n*n entries): coeffs[b][k] = sat_int16(round_half_away(
+ * BLOCK[k] / q[k])).  Prepares int16 input for the quantised grouped path. */
+dctf_status dctf_forward_dct_i16(const uint8_t *image, int height, int width,
+                                 int64_t pitch, int n, const uint16_t *q,
+                                 int16_t *coeffs, dctf_stream_t stream);
 
 /* Inverse of dctf_forward_dct followed by the uint8 conversion of Sec. III:
  * block = C^T BLOCK C (Eq. 3), rounded half away from zero and saturated to

@@ -16,11 +16,12 @@ import numpy as np
 __all__ = [
     "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3",
     "DctfError", "load", "lib_path", "exported_symbols", "build_operator", "Operator",
-    "apply", "apply_f64in", "apply_host", "forward_dct", "inverse_dct_u8", "last_error",
-    "version",
+    "apply", "apply_f64in", "apply_host", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
+    "version", "IO_F32", "IO_I16", "Group", "group_create", "apply_grouped", "Server",
 ]
 
 ZERO, REPLICATE = 0, 1
+IO_F32, IO_I16 = 0, 1
 FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3 = 0, 1, 2, 3, 4
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ETIMEOUT",
            6: "EUNSUPPORTED"}
@@ -43,8 +44,16 @@ _SIGS = {
     "dctf_apply_host": (_i32, [_vp, _vp, _i64, _vp]),
     "dctf_forward_dct": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
     "dctf_forward_dct_f64": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
+    "dctf_forward_dct_i16": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp, _vp]),
     "dctf_inverse_dct_u8": (_i32, [_vp, _i32, _i32, _i32, _vp, _i64, _vp]),
     "dctf_build_matrix_noalloc": (_i32, [_vp, _i32, _i32, _vp, _i32, _i32, _vp, _vp, _vp]),
+    "dctf_group_create": (_i32, [_vp, _i32, _i32, _vp]),
+    "dctf_group_launch": (_i32, [_vp, _vp]),
+    "dctf_group_tune": (_i32, [_vp, _vp, _i32]),
+    "dctf_group_config": (_i32, [_vp, _vp, _vp]),
+    "dctf_group_status": (_i32, [_vp, _vp, _i32]),
+    "dctf_group_destroy": (None, [_vp]),
+    "dctf_apply_grouped": (_i32, [_vp, _i32, _i32, _vp]),
     "dctf_last_error": (ctypes.c_char_p, []),
     "dctf_version": (_i32, []),
 }
@@ -181,6 +190,13 @@ def forward_dct(image, height: int, width: int, n: int, coeffs, pitch: int | Non
     _check(fn(_ptr(image), height, width, pitch or width, n, _ptr(coeffs), _stream(stream)))
 
 
+def forward_dct_i16(image, height: int, width: int, n: int, q, coeffs,
+                    pitch: int | None = None, stream=None) -> None:
+    """Device uint8 image -> int16 quantised coefficients with table q (device)."""
+    _check(load().dctf_forward_dct_i16(_ptr(image), height, width, pitch or width, n, _ptr(q),
+                                       _ptr(coeffs), _stream(stream)))
+
+
 def inverse_dct_u8(coeffs, height: int, width: int, n: int, image, pitch: int | None = None,
                    stream=None) -> None:
     """Device FP32 coefficients -> uint8 image (rounded half away, saturated)."""
@@ -191,3 +207,157 @@ def inverse_dct_u8(coeffs, height: int, width: int, n: int, image, pitch: int | 
 def apply_host(op: Operator, host_in, nblocks: int, host_out) -> None:
     """Host buffers in and out; copies and compute pipelined inside the library."""
     _check(load().dctf_apply_host(op.handle, _ptr(host_in), nblocks, _ptr(host_out)))
+
+
+class _GroupItem(ctypes.Structure):
+    _fields_ = [("op", _vp), ("inp", _vp), ("out", _vp), ("nblocks", _i64),
+                ("q_in", _vp), ("q_out", _vp)]
+
+
+def _items_array(items):
+    """items: sequence of (op, in, out, nblocks[, q_in, q_out])."""
+    arr = (_GroupItem * max(1, len(items)))()
+    for i, it in enumerate(items):
+        op, inp, out, nb = it[:4]
+        qi = it[4] if len(it) > 4 else None
+        qo = it[5] if len(it) > 5 else None
+        arr[i] = _GroupItem(op.handle, _ptr(inp), _ptr(out), int(nb), _ptr(qi), _ptr(qo))
+    return arr
+
+
+class Group:
+    """A persistent grouped launch plan (dctf_group)."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep          # the operators must outlive the group
+
+    def launch(self, stream=None) -> None:
+        _check(load().dctf_group_launch(self.handle, _stream(stream)))
+
+    def tune(self, reps: int = 5, stream=None) -> None:
+        _check(load().dctf_group_tune(self.handle, _stream(stream), reps))
+
+    def config(self) -> tuple[int, int]:
+        g, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().dctf_group_config(self.handle, ctypes.addressof(g), ctypes.addressof(r)))
+        return g.value, r.value
+
+    def status(self, clear: bool = False) -> int:
+        code = ctypes.c_uint32(0)
+        _check(load().dctf_group_status(self.handle, ctypes.addressof(code), int(clear)))
+        return code.value
+
+    def destroy(self) -> None:
+        if self.handle:
+            load().dctf_group_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def group_create(items, io: int = IO_F32) -> Group:
+    arr = _items_array(items)
+    h = ctypes.c_void_p(0)
+    _check(load().dctf_group_create(ctypes.addressof(arr), len(items), io, ctypes.addressof(h)))
+    return Group(h.value, [it[0] for it in items])
+
+
+def apply_grouped(items, io: int = IO_F32, stream=None) -> None:
+    arr = _items_array(items)
+    _check(load().dctf_apply_grouped(ctypes.addressof(arr), len(items), io, _stream(stream)))
+
+
+# ------------------------------------------------------------------ serving
+class _ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", _i32),
+                ("max_batch_requests", _i32), ("op_cache_capacity", _i32),
+                ("inject_build_failure_every", _i32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("nplanes", _i32), ("inp", _vp * 4), ("out", _vp * 4), ("nblocks", _i64 * 4),
+                ("q", _vp * 4), ("mask", _vp), ("mh", _i32), ("mw", _i32),
+                ("anchor", _i32 * 2), ("boundary", _i32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("blocks", ctypes.c_uint64), ("cache_hits", ctypes.c_uint64),
+                ("cache_misses", ctypes.c_uint64), ("max_batch_requests_seen", _i32),
+                ("hbm_in_use", ctypes.c_size_t)]
+
+
+_SIGS.update({
+    "dctf_server_create": (_i32, [_vp, _vp]),
+    "dctf_server_submit": (_i32, [_vp, _vp, _vp]),
+    "dctf_server_wait": (_i32, [_vp, ctypes.c_uint64, _i32]),
+    "dctf_server_stats": (_i32, [_vp, _vp]),
+    "dctf_server_destroy": (None, [_vp]),
+})
+
+
+class Server:
+    """Continuous-batching server for int16 quantised 8x8-block planes."""
+
+    def __init__(self, hbm_budget_bytes: int = 1 << 30, max_inflight: int = 3,
+                 max_batch_requests: int = 16, op_cache_capacity: int = 64,
+                 inject_build_failure_every: int = 0):
+        cfg = _ServerCfg(hbm_budget_bytes, max_inflight, max_batch_requests, op_cache_capacity,
+                         inject_build_failure_every)
+        h = ctypes.c_void_p(0)
+        _check(load().dctf_server_create(ctypes.addressof(cfg), ctypes.addressof(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int) -> int:
+        """planes_in/out: host int16 arrays [nblocks][64] (kept alive until wait);
+        qtabs: uint16 [64] per plane."""
+        r = _Request()
+        r.nplanes = len(planes_in)
+        keep = [np.ascontiguousarray(mask, dtype=np.float64)]
+        for p, (xi, xo, q) in enumerate(zip(planes_in, planes_out, qtabs)):
+            q = np.ascontiguousarray(q, dtype=np.uint16).ravel()
+            keep += [xi, xo, q]
+            r.inp[p] = _ptr(xi)
+            r.out[p] = _ptr(xo)
+            r.nblocks[p] = xi.shape[0]
+            r.q[p] = q.ctypes.data
+        r.mask = keep[0].ctypes.data
+        r.mh, r.mw = keep[0].shape
+        r.anchor[0], r.anchor[1] = anchor
+        r.boundary = boundary
+        t = ctypes.c_uint64(0)
+        _check(load().dctf_server_submit(self.handle, ctypes.addressof(r), ctypes.addressof(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> None:
+        st = load().dctf_server_wait(self.handle, ticket, timeout_ms)
+        if st != 5:                       # a timed-out ticket stays valid
+            self._keep.pop(ticket, None)
+        _check(st)
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(load().dctf_server_stats(self.handle, ctypes.addressof(s)))
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def close(self) -> None:
+        if self.handle:
+            load().dctf_server_destroy(self.handle)
+            self.handle = 0
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

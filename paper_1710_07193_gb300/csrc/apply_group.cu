@@ -1,0 +1,590 @@
+// Persistent grouped tensor-core apply: many (image, operator) items, one
+// launch.  y_b = M_item x_b for every block b of every item (Eq. 11 / 20).
+//
+// The batched product Y[b][n] = sum_k X[b][k] M[n][k] is a GEMM with M = 128
+// blocks per tile, N = 64 outputs, K = 64 inputs.  It moves 512 bytes per
+// block for 8192 flops, so it is bound by HBM; the tensor cores only have to
+// keep up, which leaves room for a 3-product split that restores FP32-level
+// accuracy from FP16 operands:
+//   x = x_hi + x_lo, M 2^s = M_hi + M_lo (FP16, round to nearest),
+//   y = (x_hi M_hi + x_hi M_lo + x_lo M_hi) 2^-s + M[:,0] x[0],
+// accumulated in FP32 in TMEM.  The input DC coefficient x[0] (by far the
+// largest) is kept out of the split and the long sums and applied in FP32 in
+// the epilogue, which keeps pixel errors near 1e-5.  dctf_apply runs this
+// kernel with one item; the grouped entry points with many.  Features:
+//
+//  * Work items.  Each item has its own operator (B pieces and M[:,0] in
+//    global memory), its own coefficient arrays (TMA tensor maps kept in the
+//    item descriptor), and, for quantised I/O, its own quantisation tables.
+//  * Balanced contiguous schedule.  The blocks of all items form one sequence
+//    of 64-block half tiles; CTA c takes the contiguous range
+//    [c H / G, (c+1) H / G).  Inside an item, consecutive halves pair up into
+//    128-row MMA tiles; a range or item boundary can leave a 64-row tile.
+//    The part of a range inside one item is a "segment".
+//  * Operator slots.  A loader warp copies each segment's B pieces, M[:,0]
+//    and quantisation tables into one of two shared-memory slots
+//    (cp.async.bulk), one segment ahead, so operator switches overlap the
+//    previous segment's tiles.
+//  * Quantised I/O (IoT = int16_t): the converter dequantises x = Q q_in
+//    before the split, the epilogue requantises round_half_away(y / q_out)
+//    with int16 saturation, so int16 coefficients go HBM -> HBM directly.
+//
+// Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM
+// allocator, warp 3 slot loader, warps 4-7 converter (thread = tile row),
+// warps 8-11 epilogue (each warp stores its own 32 rows).  TMEM holds a ring
+// of four [A_hi 32 | A_lo 32 | D 64] column buffers, so the MMA can run up to
+// four tiles ahead of the epilogue, which frees its buffer right after one
+// paired TMEM load.  Every wait is bounded (see sm100_ptx.cuh); waits in
+// multi-lane roles are warp-uniform.
+#include "apply_group.cuh"
+
+#include <mutex>
+
+namespace dctf {
+namespace {
+
+using namespace ptx;
+
+constexpr int kThreads = 384;
+constexpr int kTile = 128;
+constexpr int kHalf = 64;
+constexpr int kN2 = 64;
+constexpr uint32_t kTmemCols = 512;
+
+template <typename IoT> struct Io;
+template <> struct Io<float> {
+  static constexpr int kRowBytes = kN2 * 4;                 // 256
+  static constexpr int kBoxCols = 32;                       // 128-byte swizzle rows
+  static constexpr int kBoxesPerRow = 2;
+};
+template <> struct Io<int16_t> {
+  static constexpr int kRowBytes = kN2 * 2;                 // 128
+  static constexpr int kBoxCols = 64;
+  static constexpr int kBoxesPerRow = 1;
+};
+
+constexpr int kBufs = 4;        // TMEM ring: [A_hi 32 | A_lo 32 | D 64] columns each
+constexpr int kDcRing = 2 * kBufs;
+
+// S input stages, NS operator slots (1 for a single item, 2 for groups)
+template <typename IoT, int S, int NS> struct Layout {
+  static constexpr int kStageBytes = kTile * Io<IoT>::kRowBytes;
+  static constexpr int kBoxBytes = kTile * 128;              // one 128-row box
+  static constexpr int kSlabBytes = 32 * Io<IoT>::kRowBytes; // one warp's output rows
+  static constexpr int kSlabBoxBytes = 32 * 128;
+  static constexpr int kOffIn = 0;
+  static constexpr int kOffOut = kOffIn + S * kStageBytes;
+  static constexpr int kOffSlot = kOffOut + 2 * kStageBytes;
+  static constexpr int kOffDc = kOffSlot + NS * kSlotBytes;
+  static constexpr int kOffBar = kOffDc + kDcRing * kTile * 4;
+  static constexpr int kNumBars = 2 * S + 3 * kBufs + kDcRing + 2 * NS;
+  static constexpr int kOffMisc = kOffBar + kNumBars * 8;
+  static constexpr int kSmem = kOffMisc + 16 + 1024;
+  static_assert(kSmem <= 232448, "shared memory");
+};
+
+enum : uint32_t { kRoleProducer = 1, kRoleMma = 2, kRoleConv = 3, kRoleEpi = 4, kRoleDrain = 5,
+                  kRoleLoader = 6 };
+
+struct Tile {
+  int item;
+  int seg;
+  bool seg_first, seg_last;
+  int row0;      // first block of the tile inside its item
+  int rows;      // 64 or 128
+};
+
+// Walks this CTA's tiles; every role runs its own copy and sees the same
+// sequence.  Contiguous mode (groups): CTA c owns half tiles
+// [c H / G, (c+1) H / G), pairing them into 128-row tiles inside each item.
+// Interleaved mode (one item): full 128-row tiles are dealt round-robin
+// (tile k of CTA c is tile k G + c) while every CTA gets one; the remaining
+// halves are dealt one per CTA, so no CTA carries more than half a tile of
+// extra work.
+struct TileWalk {
+  const GroupItem *items;
+  int nitems;
+  int64_t h, h1;          // contiguous mode: current / end half index (global)
+  int max_take;           // halves per tile: 2 (128-row tiles) or 1 (64-row tiles)
+  bool interleaved;
+  int64_t k, full_rounds, rem_base, H;   // interleaved mode
+  int rem_step;
+  int item;
+  int64_t ih0, ih1;       // current item's global half range
+  int seg;
+  int64_t seg_h0;
+  bool started;
+
+  __device__ void init(const GroupItem *it, int n, int64_t total, int take, bool inter) {
+    items = it;
+    nitems = n;
+    max_take = take;
+    interleaved = inter;
+    seg = 0;
+    started = false;
+    if (interleaved) {
+      H = total;
+      const int64_t G = gridDim.x;
+      full_rounds = take == 2 ? H / (2 * G) : 0;
+      k = 0;
+      rem_base = full_rounds * 2 * G;
+      rem_step = 0;
+      item = 0;
+      load_item();
+      return;
+    }
+    h = total * blockIdx.x / gridDim.x;
+    h1 = total * (blockIdx.x + 1) / gridDim.x;
+    // the item holding half h (half_begin is increasing)
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (items[mid].half_begin <= h) lo = mid; else hi = mid - 1;
+    }
+    item = lo;
+    load_item();
+    seg_h0 = h;
+  }
+  __device__ void load_item() {
+    ih0 = items[item].half_begin;
+    ih1 = ih0 + (items[item].nblocks + kHalf - 1) / kHalf;
+  }
+  __device__ bool next_interleaved(Tile &t) {
+    const int64_t G = gridDim.x;
+    int64_t half;
+    int take;
+    if (k < full_rounds) {
+      half = 2 * (k * G + blockIdx.x);
+      take = 2;
+      ++k;
+    } else {
+      half = rem_base + blockIdx.x + (int64_t)rem_step * G;
+      if (half >= H) return false;
+      take = 1;
+      ++rem_step;
+    }
+    t.item = 0;
+    t.seg = 0;
+    t.seg_first = !started;
+    started = true;
+    t.row0 = (int)(half * kHalf);
+    t.rows = take * kHalf;
+    // last tile of this CTA?
+    bool more;
+    if (k < full_rounds) more = true;
+    else more = rem_base + blockIdx.x + (int64_t)rem_step * G < H;
+    t.seg_last = !more;
+    return true;
+  }
+  __device__ bool next(Tile &t) {
+    if (interleaved) return next_interleaved(t);
+    if (h >= h1) return false;
+    while (h >= ih1) {          // skips items without blocks as well
+      if (item + 1 >= nitems) return false;
+      ++item;
+      load_item();
+      ++seg;
+      seg_h0 = h;
+    }
+    const int64_t end = ih1 < h1 ? ih1 : h1;
+    const int take = (end - h >= 2 && max_take == 2) ? 2 : 1;
+    t.item = item;
+    t.seg = seg;
+    t.seg_first = (h == seg_h0);
+    t.row0 = (int)((h - ih0) * kHalf);
+    t.rows = take * kHalf;
+    h += take;
+    t.seg_last = (h == end);
+    return true;
+  }
+};
+
+// FP32 I/O: at most 152 registers a thread (58,368 of the SM's 65,536 for 384
+// threads), so the small FP64 operator-build kernels of the next image can
+// run on the same SMs while this kernel streams.
+template <typename IoT, int S, int NS, bool kGroup>
+__global__ void __maxnreg__(sizeof(IoT) == 4 ? 152 : 168)
+apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__ GroupItem single,
+                   int nitems, int64_t total_halves, int max_take, int interleaved,
+                   uint32_t *__restrict__ err) {
+  using L = Layout<IoT, S, NS>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *s_in = base + L::kOffIn;
+  uint8_t *s_out = base + L::kOffOut;
+  uint8_t *s_slot = base + L::kOffSlot;
+  float *s_dc = reinterpret_cast<float *>(base + L::kOffDc);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + L::kOffBar);
+  uint64_t *full_in = bars;                    // [S]    TMA -> converter
+  uint64_t *empty_in = bars + S;               // [S]    converter -> TMA
+  uint64_t *a_full = bars + 2 * S;             // [4]    converter -> MMA
+  uint64_t *mma_done = a_full + kBufs;         // [4]    MMA -> converter (A free), epilogue (D full)
+  uint64_t *d_empty = mma_done + kBufs;        // [4]    epilogue -> MMA
+  uint64_t *dc_full = d_empty + kBufs;         // [8]    converter -> epilogue (DC values)
+  uint64_t *slot_full = dc_full + kDcRing;     // [NS]   loader -> all
+  uint64_t *slot_empty = slot_full + NS;       // [NS]   all -> loader
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(base + L::kOffMisc);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(base + L::kOffMisc + 4);
+
+  const GroupItem *items = kGroup ? gitems : &single;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) { mbar_init(&full_in[s], 1); mbar_init(&empty_in[s], 128); }
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(&a_full[b], 128); mbar_init(&mma_done[b], 1); mbar_init(&d_empty[b], 128);
+    }
+    for (int r = 0; r < kDcRing; ++r) mbar_init(&dc_full[r], 128);
+    for (int k = 0; k < NS; ++k) { mbar_init(&slot_full[k], 1); mbar_init(&slot_empty[k], 257); }
+    *s_abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 2) { tmem_alloc(s_tmem, kTmemCols); tmem_relinquish(); }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  TileWalk walk;
+  walk.init(items, nitems, total_halves, max_take, interleaved != 0);
+  Tile t;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    int it = 0, issued = 0;
+    while (walk.next(t)) {
+      const int s = it % S;
+      const uint32_t ph = (it / S) & 1;
+      if (!wait_bounded(&empty_in[s], ph ^ 1, s_abort, err, kRoleProducer | (it << 8))) break;
+      const GroupItem &gi = items[t.item];
+      const void *map = t.rows == kTile ? (const void *)&gi.tm_in : (const void *)&gi.tm_in_half;
+      mbar_arrive_expect_tx(&full_in[s], t.rows * Io<IoT>::kRowBytes);
+      uint8_t *dst = s_in + s * L::kStageBytes;
+#pragma unroll
+      for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
+        tma_load_2d(map, &full_in[s], dst + bx * L::kBoxBytes, bx * Io<IoT>::kBoxCols, t.row0);
+      ++issued;
+      ++it;
+    }
+    for (int q = issued > S ? issued - S : 0; q < issued; ++q)
+      wait_drain(&full_in[q % S], (q / S) & 1, err, kRoleDrain);
+  } else if (warp == 3 && lane == 0) {
+    // ---------------------------------------------------------- slot loader
+    int last = -1;
+    while (walk.next(t)) {
+      if (!t.seg_first) continue;
+      const int k = t.seg % NS;
+      const int use = t.seg / NS;                 // how many times slot k was filled before
+      if (use >= 1 &&
+          !wait_bounded(&slot_empty[k], (use - 1) & 1, s_abort, err, kRoleLoader))
+        break;
+      const GroupItem &gi = items[t.item];
+      uint8_t *slot = s_slot + k * kSlotBytes;
+      const uint32_t bytes = kSlotPieces + kSlotMdc + (Io<IoT>::kBoxesPerRow == 1 ? 2 * kSlotQ : 0);
+      mbar_arrive_expect_tx(&slot_full[k], bytes);
+      bulk_load(slot, gi.pieces, kSlotPieces, &slot_full[k]);
+      bulk_load(slot + kSlotPieces, gi.mdc, kSlotMdc, &slot_full[k]);
+      if (Io<IoT>::kBoxesPerRow == 1) {
+        bulk_load(slot + kSlotPieces + kSlotMdc, gi.qin, kSlotQ, &slot_full[k]);
+        bulk_load(slot + kSlotPieces + kSlotMdc + kSlotQ, gi.qout, kSlotQ, &slot_full[k]);
+      }
+      last = t.seg;
+    }
+    for (int sg = last - NS + 1 > 0 ? last - NS + 1 : 0; sg <= last; ++sg)
+      wait_drain(&slot_full[sg % NS], (sg / NS) & 1, err, kRoleDrain);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
+    // D (64 columns) = A_hi M_lo^T + A_lo M_hi^T + A_hi M_hi^T, 12 MMAs of
+    // 128 x 64 x 16; the three products share one FP32 accumulator.
+    constexpr uint32_t kIdesc = idesc_f16(128, kN2, false);
+    int it = 0, last = -1;
+    while (walk.next(t)) {
+      const int b = it % kBufs, k = t.seg % NS;
+      const uint32_t ph = (it / kBufs) & 1;
+      if (t.seg_first &&
+          !wait_bounded(&slot_full[k], (t.seg / NS) & 1, s_abort, err, kRoleMma | (it << 8)))
+        break;
+      if (!wait_bounded(&a_full[b], ph, s_abort, err, kRoleMma | (it << 8))) break;
+      if (!wait_bounded(&d_empty[b], ph ^ 1, s_abort, err, kRoleMma | (it << 8))) break;
+      tc_fence_after();
+      const uint64_t b_hi = desc_sw128(smem_u32(s_slot + k * kSlotBytes));
+      const uint64_t b_lo = desc_sw128(smem_u32(s_slot + k * kSlotBytes + kN2 * 128));
+      const uint32_t t_a = tmem + b * 128, t_d = t_a + 64;
+      // the two small correction products first, so they accumulate at
+      // their own magnitude before the main product is added
+#pragma unroll
+      for (int kk = 0; kk < kN2 / 16; ++kk)
+        mma_f16_ts(t_d, t_a + 8 * kk, b_lo + 2 * kk, kIdesc, kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < kN2 / 16; ++kk)
+        mma_f16_ts(t_d, t_a + 32 + 8 * kk, b_hi + 2 * kk, kIdesc, 1);
+#pragma unroll
+      for (int kk = 0; kk < kN2 / 16; ++kk)
+        mma_f16_ts(t_d, t_a + 8 * kk, b_hi + 2 * kk, kIdesc, 1);
+      tc_commit(&mma_done[b]);
+      if (t.seg_last) tc_commit(&slot_empty[k]);   // slot free once these MMAs finish
+      last = it;
+      ++it;
+    }
+    if (last >= 0) wait_drain(&mma_done[last % kBufs], (last / kBufs) & 1, err, kRoleDrain);
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------------------------------------------------- converter
+    const int row = tid - 128;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    int it = 0;
+    while (walk.next(t)) {
+      const int s = it % S, b = it % kBufs, r = it % kDcRing, k = t.seg % NS;
+      const uint32_t ps = (it / S) & 1, pb = (it / kBufs) & 1;
+      // every role that releases a slot first waits for it to be filled, so
+      // its release can never count toward the slot's previous use
+      if (t.seg_first &&
+          !warp_wait_bounded(&slot_full[k], (t.seg / NS) & 1, s_abort, err, kRoleConv | (it << 8)))
+        break;
+      if (!warp_wait_bounded(&full_in[s], ps, s_abort, err, kRoleConv | (it << 8))) break;
+      float v[64];
+      const uint8_t *st = s_in + s * L::kStageBytes + row * 128;
+      if constexpr (Io<IoT>::kBoxesPerRow == 2) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const float4 q = *reinterpret_cast<const float4 *>(
+              st + (u >> 3) * L::kBoxBytes + (((u & 7) ^ (row & 7)) << 4));
+          v[4 * u] = q.x; v[4 * u + 1] = q.y; v[4 * u + 2] = q.z; v[4 * u + 3] = q.w;
+        }
+      } else {
+        // quantised input: x = Q * q_in (exact in FP32)
+        const uint16_t *qin = reinterpret_cast<const uint16_t *>(
+            s_slot + k * kSlotBytes + kSlotPieces + kSlotMdc);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint4 q = *reinterpret_cast<const uint4 *>(st + (((u & 7) ^ (row & 7)) << 4));
+          const uint4 qq = *reinterpret_cast<const uint4 *>(qin + 8 * u);
+          const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+          const uint32_t m[4] = {qq.x, qq.y, qq.z, qq.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            v[8 * u + 2 * e] = (float)(int16_t)(w[e] & 0xffffu) * (float)(m[e] & 0xffffu);
+            v[8 * u + 2 * e + 1] = (float)(int16_t)(w[e] >> 16) * (float)(m[e] >> 16);
+          }
+        }
+      }
+      mbar_arrive(&empty_in[s]);
+      if (row >= t.rows) {
+#pragma unroll
+        for (int c = 0; c < 64; ++c) v[c] = 0.f;     // rows past the tile: not stored
+      }
+      const float x0 = v[0];
+      v[0] = 0.f;
+      // A buffer b is free once the MMAs of tile it - kBufs completed
+      if (!warp_wait_bounded(&mma_done[b], pb ^ 1, s_abort, err, kRoleConv | (it << 8))) break;
+      s_dc[r * kTile + row] = x0;
+      mbar_arrive(&dc_full[r]);
+      tc_fence_after();
+      const uint32_t t_a = tmem + lane_base + b * 128;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float a0 = v[32 * h + 2 * c], a1 = v[32 * h + 2 * c + 1];
+          const __half2 h2 = __floats2half2_rn(a0, a1);     // .x (low half) = element 2c
+          const float2 hf = __half22float2(h2);
+          const __half2 l2 = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
+          hi[c] = *reinterpret_cast<const uint32_t *>(&h2);
+          lo[c] = *reinterpret_cast<const uint32_t *>(&l2);
+        }
+        tmem_st16(t_a + 16 * h, hi);
+        tmem_st16(t_a + 32 + 16 * h, lo);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      mbar_arrive(&a_full[b]);
+      if (t.seg_last) mbar_arrive(&slot_empty[k]);
+      ++it;
+    }
+  } else if (warp >= 8) {
+    // ---------------------------------------------------------- epilogue
+    const int row = tid - 256, wr = warp & 3, r32 = lane;
+    const uint32_t lane_base = (uint32_t)(wr * 32) << 16;
+    int it = 0;
+    while (walk.next(t)) {
+      const int b = it % kBufs, o = it & 1, r = it % kDcRing, k = t.seg % NS;
+      const uint32_t pb = (it / kBufs) & 1, pr = (it / kDcRing) & 1;
+      if (t.seg_first &&
+          !warp_wait_bounded(&slot_full[k], (t.seg / NS) & 1, s_abort, err, kRoleEpi | (it << 8)))
+        break;
+      if (!warp_wait_bounded(&mma_done[b], pb, s_abort, err, kRoleEpi | (it << 8))) break;
+      tc_fence_after();
+      float acc[64];
+      {
+        uint32_t d0[32], d1[32];
+        tmem_ld32x2(tmem + lane_base + b * 128 + 64, tmem + lane_base + b * 128 + 96, d0, d1);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          acc[c] = __uint_as_float(d0[c]);
+          acc[32 + c] = __uint_as_float(d1[c]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&d_empty[b]);                      // D[b] may be overwritten now
+      if (!warp_wait_bounded(&dc_full[r], pr, s_abort, err, kRoleEpi | (it << 8))) break;
+      const float x0 = s_dc[r * kTile + row];
+      const GroupItem &gi = items[t.item];
+      const float out_scale = gi.out_scale;
+      const uint8_t *slot = s_slot + k * kSlotBytes;
+      const float4 *mdc4 = reinterpret_cast<const float4 *>(slot + kSlotPieces);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const float4 md = mdc4[u];
+        acc[4 * u] = fmaf(acc[4 * u], out_scale, md.x * x0);
+        acc[4 * u + 1] = fmaf(acc[4 * u + 1], out_scale, md.y * x0);
+        acc[4 * u + 2] = fmaf(acc[4 * u + 2], out_scale, md.z * x0);
+        acc[4 * u + 3] = fmaf(acc[4 * u + 3], out_scale, md.w * x0);
+      }
+      const bool store = wr * 32 < t.rows;
+      if (lane == 0) bulk_wait_read<1>();             // slab o free (store of tile it-2 read it)
+      __syncwarp();
+      uint8_t *slab = s_out + o * L::kStageBytes + wr * L::kSlabBytes;
+      if constexpr (Io<IoT>::kBoxesPerRow == 2) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          *reinterpret_cast<float4 *>(slab + (u >> 3) * L::kSlabBoxBytes + r32 * 128 +
+                                      (((u & 7) ^ (r32 & 7)) << 4)) =
+              make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+      } else {
+        // requantise: round_half_away(y / q_out), saturated to int16
+        const uint16_t *qout = reinterpret_cast<const uint16_t *>(
+            slot + kSlotPieces + kSlotMdc + kSlotQ);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint4 qq = *reinterpret_cast<const uint4 *>(qout + 8 * u);
+          const uint32_t m[4] = {qq.x, qq.y, qq.z, qq.w};
+          uint32_t w[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float a = roundf(__fdiv_rn(acc[8 * u + 2 * e], (float)(m[e] & 0xffffu)));
+            float c = roundf(__fdiv_rn(acc[8 * u + 2 * e + 1], (float)(m[e] >> 16)));
+            a = fminf(fmaxf(a, -32768.f), 32767.f);
+            c = fminf(fmaxf(c, -32768.f), 32767.f);
+            w[e] = ((uint32_t)(uint16_t)(int16_t)a) | ((uint32_t)(uint16_t)(int16_t)c << 16);
+          }
+          *reinterpret_cast<uint4 *>(slab + r32 * 128 + ((u ^ (r32 & 7)) << 4)) =
+              make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's M[:,0], q_out
+      if (lane == 0) {
+        if (store) {
+          const int y0 = t.row0 + wr * 32;
+#pragma unroll
+          for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
+            tma_store_2d(&gi.tm_out, slab + bx * L::kSlabBoxBytes, bx * Io<IoT>::kBoxCols, y0);
+        }
+        bulk_commit();
+      }
+      ++it;
+    }
+    if (lane == 0) bulk_wait<0>();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// [nblocks][64] rows (FP32 or int16) as a 2-D tensor; boxes of 128 bytes
+// (32 floats or 64 int16) x box_rows rows, 128-byte swizzle.
+cudaError_t make_map(CUtensorMap *m, const void *ptr, int64_t nblocks, bool i16, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return cudaErrorNotSupported;
+  const int esz = i16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)kN2, (cuuint64_t)nblocks};
+  cuuint64_t strides[1] = {(cuuint64_t)kN2 * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, i16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void *>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename IoT, int S, int NS, bool kGroup>
+cudaError_t launch_cfg(const GroupItem *d_items, const GroupItem &single, int nitems,
+                       int64_t total_halves, int grid, int max_take, int interleaved,
+                       uint32_t *err, cudaStream_t s) {
+  auto kern = apply_group_kernel<IoT, S, NS, kGroup>;
+  constexpr int smem = Layout<IoT, S, NS>::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, s>>>(d_items, single, nitems, total_halves, max_take, interleaved,
+                                    err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *in, void *out,
+                            int64_t nblocks, bool i16, const uint16_t *qin,
+                            const uint16_t *qout) {
+  memset(gi, 0, sizeof *gi);
+  cudaError_t e = make_map(&gi->tm_in, in, nblocks, i16, kTile);
+  if (e == cudaSuccess) e = make_map(&gi->tm_in_half, in, nblocks, i16, kHalf);
+  if (e == cudaSuccess) e = make_map(&gi->tm_out, out, nblocks, i16, 32);
+  if (e != cudaSuccess) return e;
+  gi->pieces = op->d_f16;
+  gi->mdc = op->d_Mdc;
+  gi->qin = qin;
+  gi->qout = qout;
+  gi->out_scale = ldexpf(1.0f, -op->f16_scale_exp);
+  gi->nblocks = nblocks;
+  return cudaSuccess;
+}
+
+cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
+                               int64_t total_halves, bool i16, int grid, int max_take,
+                               uint32_t *err, cudaStream_t s) {
+  if (total_halves <= 0) return cudaSuccess;
+  int64_t g = grid > 0 ? grid : 0;
+  if (g > total_halves) g = total_halves;
+  if (g < 1) g = 1;
+  static const GroupItem kEmpty = {};
+  const int take = max_take == 1 ? 1 : 2;
+  if (single != nullptr) {   // one item: interleaved schedule, one operator slot, 4 stages
+    return i16 ? launch_cfg<int16_t, 4, 1, false>(nullptr, *single, 1, total_halves, (int)g, take,
+                                                 1, err, s)
+               : launch_cfg<float, 4, 1, false>(nullptr, *single, 1, total_halves, (int)g, take, 1,
+                                               err, s);
+  }
+  return i16 ? launch_cfg<int16_t, 4, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take,
+                                              0, err, s)
+             : launch_cfg<float, 3, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take, 0,
+                                            err, s);
+}
+
+}  // namespace dctf

@@ -1,0 +1,41 @@
+// Descriptor of one work item of the persistent grouped apply kernel.
+#pragma once
+
+#include "sm100_ptx.cuh"
+
+namespace dctf {
+
+// Per-item operator slot in shared memory: B pieces (F16X3, 8x8 blocks),
+// M[:,0], and the two quantisation tables of the int16 path.
+constexpr int kSlotPieces = 2 * 64 * 128;   // 128 rows x 128 B
+constexpr int kSlotMdc = 64 * 4;
+constexpr int kSlotQ = 64 * 2;
+constexpr int kSlotBytes = 17408;            // rounded up to 1024 (swizzle atom)
+static_assert(kSlotPieces + kSlotMdc + 2 * kSlotQ <= kSlotBytes, "slot size");
+
+struct GroupItem {              // CUtensorMap members keep it 128-byte aligned
+  CUtensorMap tm_in;        // 128-row boxes
+  CUtensorMap tm_in_half;   // 64-row boxes (tiles at range / item ends)
+  CUtensorMap tm_out;       // 32-row boxes (one per epilogue warp)
+  const void *pieces;       // FP16 hi/lo B image (16 KB, SWIZZLE_128B layout)
+  const float *mdc;         // M[:, 0], FP32
+  const uint16_t *qin;      // quantisation table of the input (int16 path)
+  const uint16_t *qout;     // quantisation table of the output (int16 path)
+  float out_scale;          // 2^-s of the pieces
+  int pad0;
+  int64_t nblocks;
+  int64_t half_begin;       // first 64-block half tile of the item in the group
+};
+
+cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *in, void *out,
+                            int64_t nblocks, bool i16, const uint16_t *qin,
+                            const uint16_t *qout);
+
+// d_items: device array (group mode, single == nullptr) or single: one item
+// passed by value.  grid <= 0 means one CTA per SM.  max_take: 2 for 128-row
+// tiles, 1 for 64-row tiles.
+cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
+                               int64_t total_halves, bool i16, int grid, int max_take,
+                               uint32_t *err, cudaStream_t s);
+
+}  // namespace dctf

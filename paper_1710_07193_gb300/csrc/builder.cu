@@ -47,21 +47,36 @@ __device__ inline double dct2_vec(const double *in, double *tmp,
   return r;
 }
 
-__global__ void build_hg_kernel(const MaskParams mp, double *__restrict__ H,
-                                double *__restrict__ G) {
+// C (Eq. 1-2) into global memory, once per operator: the FP64 cosines are
+// costly on this part, so the per-mask build kernels only copy the table.
+__global__ void dct_matrix_kernel(int n, double *__restrict__ C) {
+  const int t = threadIdx.x;
+  if (t < n * n) {
+    int u = t / n, x = t % n;
+    double alpha = (u == 0) ? sqrt(1.0 / n) : sqrt(2.0 / n);
+    C[t] = alpha * cos(M_PI * (2 * x + 1) * u / (2 * n));
+  }
+}
+
+__device__ inline void load_c(double (*cs)[kMaxN + 1], const double *__restrict__ C, int n) {
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) cs[t / n][t % n] = C[t];
+}
+
+__global__ void build_hg_kernel(const MaskParams mp, const double *__restrict__ C,
+                                double *__restrict__ H, double *__restrict__ G) {
   __shared__ double cs[kMaxN][kMaxN + 1];
   __shared__ double hrow[kMaxN2];
   __shared__ double tmp[kMaxN2];
   const int n = mp.n, n2 = n * n, p = blockIdx.x, t = threadIdx.x;
   const int i = p / n, j = p % n;
-  dct_matrix_smem(cs, n);
-  if (t < n2) hrow[t] = 0.0;
-  __syncthreads();
-  if (t == 0) {
+  load_c(cs, C, n);
+  if (t < n2) {
     // Row (i, j) of H: mask entry (r, c) reads pixel (i + r - ar, j + c - ac)
     // of the same block (Eq. 5 as a correlation); zero padding drops the
     // pixels outside the block (Sec. II.B), border replication moves them to
     // the nearest edge pixel, clamping each axis (Sec. II.C, Eq. 13-18).
+    // Thread t owns column t and adds its entries in (r, c) order.
+    double acc = 0.0;
     for (int r = 0; r < mp.mh; ++r)
       for (int c = 0; c < mp.mw; ++c) {
         int s = i + r - mp.ar, u = j + c - mp.ac;
@@ -71,24 +86,26 @@ __global__ void build_hg_kernel(const MaskParams mp, double *__restrict__ H,
           s = min(max(s, 0), n - 1);
           u = min(max(u, 0), n - 1);
         }
-        hrow[s * n + u] += mp.w[r * mp.mw + c];
+        if (s * n + u == t) acc += mp.w[r * mp.mw + c];
       }
+    hrow[t] = acc;
+    H[(size_t)p * n2 + t] = acc;
   }
   __syncthreads();
-  if (t < n2) H[(size_t)p * n2 + t] = hrow[t];
   // G[p][:] = (H K^T)[p][:] = K H[p][:]^T = vec(C mat(H[p][:]) C^T)
   double g = dct2_vec(hrow, tmp, cs, n, t);
   if (t < n2) G[(size_t)p * n2 + t] = g;
 }
 
-__global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restrict__ G,
-                               double *__restrict__ M64, float *__restrict__ M32,
-                               float *__restrict__ Mdc, __half *__restrict__ f16) {
+__global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restrict__ C,
+                               const double *__restrict__ G, double *__restrict__ M64,
+                               float *__restrict__ M32, float *__restrict__ Mdc,
+                               __half *__restrict__ f16) {
   __shared__ double cs[kMaxN][kMaxN + 1];
   __shared__ double gcol[kMaxN2];
   __shared__ double tmp[kMaxN2];
   const int n2 = n * n, q = blockIdx.x, t = threadIdx.x;
-  dct_matrix_smem(cs, n);
+  load_c(cs, C, n);
   if (t < n2) gcol[t] = G[(size_t)t * n2 + q];
   __syncthreads();
   // M[:][q] = K G[:][q] = vec(C mat(G[:][q]) C^T)
@@ -112,12 +129,17 @@ __global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restric
 
 }  // namespace
 
+cudaError_t launch_dct_matrix(dctf_operator *op, cudaStream_t s) {
+  dct_matrix_kernel<<<1, op->n2, 0, s>>>(op->n, op->d_C64);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s) {
   const int n2 = op->n2;
-  build_hg_kernel<<<n2, n2, 0, s>>>(mp, op->d_H64, op->d_G64);
+  build_hg_kernel<<<n2, n2, 0, s>>>(mp, op->d_C64, op->d_H64, op->d_G64);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  build_m_kernel<<<n2, n2, 0, s>>>(op->n, op->f16_scale_exp, op->d_G64, op->d_M64,
+  build_m_kernel<<<n2, n2, 0, s>>>(op->n, op->f16_scale_exp, op->d_C64, op->d_G64, op->d_M64,
                                    op->d_M32, op->d_Mdc, op->d_f16);
   return cudaGetLastError();
 }

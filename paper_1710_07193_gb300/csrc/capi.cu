@@ -5,7 +5,7 @@
 #include <mutex>
 #include <new>
 
-#include "dctf_internal.cuh"
+#include "apply_group.cuh"
 
 namespace dctf {
 
@@ -103,7 +103,8 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   op->n = n; op->n2 = n * n;
   const size_t n2 = op->n2, sq = n2 * n2;
   const bool pieces = tc_supported(n, DCTF_F16X3);
-  size_t off = 0, o_M64, o_H64, o_G64, o_M32, o_Mdc, o_f16 = 0, o_err;
+  size_t off = 0, o_C64, o_M64, o_H64, o_G64, o_M32, o_Mdc, o_f16 = 0, o_err;
+  o_C64 = off; off = align_up(off + n2 * 8, 1024);
   o_M64 = off; off = align_up(off + sq * 8, 1024);
   o_H64 = off; off = align_up(off + sq * 8, 1024);
   o_G64 = off; off = align_up(off + sq * 8, 1024);
@@ -115,6 +116,7 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   if (e != cudaSuccess) { delete op; return cuda_error(e, "cudaMalloc(operator)"); }
   op->bytes = off;
   char *b = static_cast<char *>(op->d_base);
+  op->d_C64 = reinterpret_cast<double *>(b + o_C64);
   op->d_M64 = reinterpret_cast<double *>(b + o_M64);
   op->d_H64 = reinterpret_cast<double *>(b + o_H64);
   op->d_G64 = reinterpret_cast<double *>(b + o_G64);
@@ -126,7 +128,8 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
 
   e = cudaMemsetAsync(op->d_err, 0, 256, stream);
   if (e == cudaSuccess && pieces) e = cudaMemsetAsync(op->d_f16, 0, 2 * sq * 2, stream);
-  if (e != cudaSuccess) { dctf_release_operator(op); return cuda_error(e, "cudaMemsetAsync"); }
+  if (e == cudaSuccess) e = launch_dct_matrix(op, stream);
+  if (e != cudaSuccess) { dctf_release_operator(op); return cuda_error(e, "operator set-up"); }
   st = dctf_operator_rebuild(op, mask, mh, mw, anchor, boundary, stream);
   if (st != DCTF_OK) { dctf_release_operator(op); return st; }
   *out = op;
@@ -213,10 +216,16 @@ dctf_status dctf_apply(const dctf_operator *op, const float *coeffs, int64_t nbl
   dctf_status st = check_apply(op, coeffs, sizeof(float), nblocks, out);
   if (st != DCTF_OK || nblocks == 0) return st;
   cudaError_t e;
-  if (op->precision == DCTF_FP32_SIMT)
+  if (op->precision == DCTF_FP32_SIMT) {
     e = launch_apply_simt(op, coeffs, nullptr, nblocks, out, stream);
-  else
-    e = launch_apply_tc(op, coeffs, nblocks, out, stream);
+  } else {
+    // one item of the persistent tensor-core kernel, descriptor by value
+    GroupItem gi;
+    e = fill_group_item(&gi, op, coeffs, out, nblocks, false, nullptr, nullptr);
+    if (e == cudaSuccess)
+      e = launch_apply_group(nullptr, &gi, 1, (nblocks + 63) / 64, false, sm_count(op->device), 2,
+                             op->d_err, stream);
+  }
   if (e != cudaSuccess) return cuda_error(e, "dctf_apply launch");
   return DCTF_OK;
 }

@@ -57,6 +57,7 @@ struct dctf_operator {
   // one device allocation, carved:
   void *d_base;
   size_t bytes;
+  double *d_C64;            // [n][n] DCT matrix C (Eq. 1-2), made once at creation
   double *d_M64;            // [n2][n2] FP64 operator, row = output coefficient
   double *d_H64;            // [n2][n2] spatial operator
   double *d_G64;            // [n2][n2] scratch: H K^T
@@ -74,6 +75,7 @@ struct dctf_operator {
 namespace dctf {
 
 // builder.cu
+cudaError_t launch_dct_matrix(dctf_operator *op, cudaStream_t s);
 cudaError_t launch_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s);
 
 // apply_simt.cu
@@ -81,10 +83,8 @@ cudaError_t launch_apply_simt(const dctf_operator *op, const float *x,
                               const double *x64, int64_t nblocks, float *y,
                               cudaStream_t s);
 
-// apply_tc.cu
-bool tc_supported(int n, dctf_precision p);
-cudaError_t launch_apply_tc(const dctf_operator *op, const float *x,
-                            int64_t nblocks, float *y, cudaStream_t s);
+// apply_group.cu: tensor-core kernels exist for these (n, precision)
+inline bool tc_supported(int n, dctf_precision p) { return n == 8 && p == DCTF_F16X3; }
 
 int sm_count(int device);
 

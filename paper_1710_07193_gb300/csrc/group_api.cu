@@ -1,0 +1,256 @@
+// Grouped apply: C ABI, launch plans and the autotuner.
+//
+// A group is a list of (operator, input, output, quantisation tables)
+// items run by one persistent launch of apply_group_kernel.  Creating a
+// group encodes every item's TMA tensor maps once and uploads the
+// descriptors; launching it is then a single kernel launch with no host work,
+// so it can be captured in a CUDA graph and replayed.
+//
+// Autotuner.  Two launch parameters matter for uneven batches: the number of
+// persistent CTAs and the tile height (128-row tiles, or 64-row tiles that
+// balance small items better).  dctf_group_tune times every candidate on the
+// group itself (CUDA events, median of `reps`) and keeps the fastest; the
+// choice is also cached per (I/O type, size class) and used as the default
+// for later groups of that class.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "apply_group.cuh"
+
+struct dctf_group {
+  int device;
+  int nitems;
+  bool i16;
+  int64_t total_halves;
+  dctf::GroupItem *d_items;
+  uint32_t *d_err;
+  int grid;        // CTAs (0: one per SM)
+  int max_take;    // 2: 128-row tiles, 1: 64-row tiles
+  bool in_place;   // some item filters in place (tuning would re-filter it)
+};
+
+namespace dctf {
+namespace {
+
+struct TuneKey {
+  bool i16;
+  int size_class;   // floor(log2(total halves))
+  bool operator<(const TuneKey &o) const {
+    return i16 != o.i16 ? i16 < o.i16 : size_class < o.size_class;
+  }
+};
+struct TuneVal { int grid_num, grid_den, max_take; };
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+int size_class(int64_t halves) {
+  int c = 0;
+  while ((halves >> (c + 1)) > 0) ++c;
+  return c;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+dctf_status check_items(const dctf_group_item *items, int nitems, dctf_io io) {
+  if (nitems < 0 || (nitems > 0 && items == nullptr))
+    return set_error(DCTF_EINVAL, "bad item list");
+  if (io != DCTF_IO_F32 && io != DCTF_IO_I16) return set_error(DCTF_EINVAL, "bad io type %d", io);
+  for (int i = 0; i < nitems; ++i) {
+    const dctf_group_item &it = items[i];
+    if (it.op == nullptr) return set_error(DCTF_EINVAL, "item %d: operator is NULL", i);
+    if (it.op->n != 8 || it.op->d_f16 == nullptr)
+      return set_error(DCTF_EUNSUPPORTED, "item %d: grouped apply needs an 8x8 operator", i);
+    if (it.nblocks < 0) return set_error(DCTF_EINVAL, "item %d: nblocks < 0", i);
+    if (it.nblocks == 0) continue;
+    if (it.in == nullptr || it.out == nullptr || !aligned16(it.in) || !aligned16(it.out))
+      return set_error(DCTF_EINVAL, "item %d: buffers must be non-NULL and 16-byte aligned", i);
+    if (it.nblocks > ((int64_t)1 << 31) - 128)
+      return set_error(DCTF_EINVAL, "item %d: nblocks too large", i);
+    const size_t bytes = (size_t)it.nblocks * 64 * (io == DCTF_IO_I16 ? 2 : 4);
+    const char *a = static_cast<const char *>(it.in);
+    const char *b = static_cast<const char *>(it.out);
+    if (a != b && a < b + bytes && b < a + bytes)
+      return set_error(DCTF_EINVAL, "item %d: input and output overlap without being equal", i);
+    if (io == DCTF_IO_I16) {
+      if (it.q_in == nullptr || it.q_out == nullptr || !aligned16(it.q_in) || !aligned16(it.q_out))
+        return set_error(DCTF_EINVAL, "item %d: int16 items need 16-byte aligned q tables", i);
+    }
+  }
+  return DCTF_OK;
+}
+
+dctf_status fill_items(const dctf_group_item *items, int nitems, dctf_io io,
+                       std::vector<GroupItem> *out, int64_t *total) {
+  out->resize(nitems > 0 ? nitems : 1);
+  int64_t h = 0;
+  for (int i = 0; i < nitems; ++i) {
+    const dctf_group_item &it = items[i];
+    GroupItem &gi = (*out)[i];
+    if (it.nblocks > 0) {
+      cudaError_t e = fill_group_item(&gi, it.op, it.in, it.out, it.nblocks, io == DCTF_IO_I16,
+                                      it.q_in, it.q_out);
+      if (e != cudaSuccess) return cuda_error(e, "tensor map encode");
+    } else {
+      memset(&gi, 0, sizeof gi);
+    }
+    gi.half_begin = h;
+    h += (it.nblocks + 63) / 64;
+  }
+  *total = h;
+  return DCTF_OK;
+}
+
+cudaError_t launch(const dctf_group *g, int grid, int max_take, cudaStream_t s) {
+  return launch_apply_group(g->d_items, nullptr, g->nitems, g->total_halves, g->i16, grid,
+                            max_take, g->d_err, s);
+}
+
+}  // namespace
+}  // namespace dctf
+
+using namespace dctf;
+
+extern "C" {
+
+dctf_status dctf_group_create(const dctf_group_item *items, int nitems, dctf_io io,
+                              dctf_group **out) {
+  if (out == nullptr) return set_error(DCTF_EINVAL, "out is NULL");
+  *out = nullptr;
+  dctf_status st = check_items(items, nitems, io);
+  if (st != DCTF_OK) return st;
+  std::vector<GroupItem> host;
+  int64_t total = 0;
+  st = fill_items(items, nitems, io, &host, &total);
+  if (st != DCTF_OK) return st;
+  dctf_group *g = new (std::nothrow) dctf_group();
+  if (g == nullptr) return set_error(DCTF_ENOMEM, "host allocation failed");
+  g->nitems = nitems;
+  g->i16 = io == DCTF_IO_I16;
+  g->total_halves = total;
+  for (int i = 0; i < nitems; ++i)
+    if (items[i].nblocks > 0 && items[i].in == items[i].out) g->in_place = true;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_items, host.size() * sizeof(GroupItem) + 256);
+  if (e == cudaSuccess) {
+    g->d_err = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(g->d_items) +
+                                            host.size() * sizeof(GroupItem));
+    e = cudaMemcpy(g->d_items, host.data(), host.size() * sizeof(GroupItem),
+                   cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, 256);
+  if (e != cudaSuccess) {
+    if (g->d_items) cudaFree(g->d_items);
+    delete g;
+    return cuda_error(e, "group descriptors");
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(TuneKey{g->i16, size_class(total)});
+    const int sms = sm_count(g->device);
+    if (it != g_tune_cache.end()) {
+      g->grid = std::max(1, sms * it->second.grid_num / it->second.grid_den);
+      g->max_take = it->second.max_take;
+    } else {
+      g->grid = 0;
+      g->max_take = 2;
+    }
+  }
+  *out = g;
+  return DCTF_OK;
+}
+
+dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream) {
+  if (g == nullptr) return set_error(DCTF_EINVAL, "group is NULL");
+  if (g->total_halves == 0) return DCTF_OK;
+  int grid = g->grid > 0 ? g->grid : sm_count(g->device);
+  cudaError_t e = launch(g, grid, g->max_take, stream);
+  if (e != cudaSuccess) return cuda_error(e, "grouped apply launch");
+  return DCTF_OK;
+}
+
+dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps) {
+  if (g == nullptr) return set_error(DCTF_EINVAL, "group is NULL");
+  if (g->total_halves == 0) return DCTF_OK;
+  if (g->in_place)
+    return set_error(DCTF_EINVAL, "tuning runs the group repeatedly: items must not be in place");
+  if (reps < 1) reps = 5;
+  const int sms = sm_count(g->device);
+  static const int kFrac[][2] = {{1, 1}, {3, 4}, {1, 2}};
+  cudaEvent_t e0, e1;
+  DCTF_CUDA(cudaEventCreate(&e0));
+  DCTF_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  TuneVal best_v{1, 1, 2};
+  for (const auto &f : kFrac) {
+    for (int take = 2; take >= 1; --take) {
+      const int grid = std::max(1, sms * f[0] / f[1]);
+      std::vector<float> ts;
+      for (int r = 0; r < reps + 1; ++r) {
+        cudaEventRecord(e0, stream);
+        cudaError_t e = launch(g, grid, take, stream);
+        cudaEventRecord(e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return cuda_error(e, "autotune launch");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) ts.push_back(ms);   // first run warms the caches
+      }
+      std::sort(ts.begin(), ts.end());
+      const float med = ts[ts.size() / 2];
+      if (med < best) { best = med; best_v = TuneVal{f[0], f[1], take}; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->grid = std::max(1, sms * best_v.grid_num / best_v.grid_den);
+  g->max_take = best_v.max_take;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[TuneKey{g->i16, size_class(g->total_halves)}] = best_v;
+  return DCTF_OK;
+}
+
+dctf_status dctf_group_config(const dctf_group *g, int *grid, int *tile_rows) {
+  if (g == nullptr) return set_error(DCTF_EINVAL, "group is NULL");
+  if (grid) *grid = g->grid > 0 ? g->grid : sm_count(g->device);
+  if (tile_rows) *tile_rows = 64 * g->max_take;
+  return DCTF_OK;
+}
+
+dctf_status dctf_group_status(dctf_group *g, uint32_t *code, int clear) {
+  if (g == nullptr || code == nullptr) return set_error(DCTF_EINVAL, "NULL argument");
+  DCTF_CUDA(cudaDeviceSynchronize());
+  DCTF_CUDA(cudaMemcpy(code, g->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (clear) DCTF_CUDA(cudaMemset(g->d_err, 0, sizeof(uint32_t)));
+  return DCTF_OK;
+}
+
+void dctf_group_destroy(dctf_group *g) {
+  if (g == nullptr) return;
+  if (g->d_items) cudaFree(g->d_items);
+  delete g;
+}
+
+dctf_status dctf_apply_grouped(const dctf_group_item *items, int nitems, dctf_io io,
+                               dctf_stream_t stream) {
+  dctf_group *g = nullptr;
+  dctf_status st = dctf_group_create(items, nitems, io, &g);
+  if (st != DCTF_OK) return st;
+  st = dctf_group_launch(g, stream);
+  // the descriptors must outlive the launch
+  cudaError_t e = cudaStreamSynchronize(stream);
+  dctf_group_destroy(g);
+  if (st != DCTF_OK) return st;
+  if (e != cudaSuccess) return cuda_error(e, "grouped apply");
+  return DCTF_OK;
+}
+
+}  // extern "C"

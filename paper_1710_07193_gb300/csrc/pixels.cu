@@ -52,6 +52,43 @@ __global__ void forward_dct_kernel(const uint8_t *__restrict__ img, int height, 
   }
 }
 
+// Forward DCT then JPEG-style quantisation: Q = sat_int16(round_half_away(
+// BLOCK / q)) with a per-coefficient table q (input preparation for the
+// quantised path).
+template <int N>
+__global__ void forward_dct_q16_kernel(const uint8_t *__restrict__ img, int height, int width,
+                                       int64_t pitch, const uint16_t *__restrict__ q,
+                                       int16_t *__restrict__ out) {
+  constexpr int N2 = N * N, BPC = blocks_per_cta<N>();
+  __shared__ double cs[N][N + 1];
+  __shared__ double xs[BPC][N2], ts[BPC][N2];
+  load_c<N>(cs);
+  const int bl = threadIdx.x / N2, t = threadIdx.x % N2, u = t / N, v = t % N;
+  const int bw = width / N;
+  const int64_t nblocks = (int64_t)(height / N) * bw;
+  const int64_t b = (int64_t)blockIdx.x * BPC + bl;
+  const bool live = b < nblocks;
+  if (live) {
+    const int64_t by = b / bw, bx = b % bw;
+    xs[bl][t] = img[(by * N + u) * pitch + bx * N + v];
+  }
+  __syncthreads();
+  if (live) {
+    double a = 0.0;
+    for (int i = 0; i < N; ++i) a += cs[u][i] * xs[bl][i * N + v];
+    ts[bl][t] = a;
+  }
+  __syncthreads();
+  if (live) {
+    double a = 0.0;
+    for (int j = 0; j < N; ++j) a += ts[bl][u * N + j] * cs[v][j];
+    double r = a / (double)q[t];
+    r = r < 0.0 ? -floor(-r + 0.5) : floor(r + 0.5);
+    r = r < -32768.0 ? -32768.0 : (r > 32767.0 ? 32767.0 : r);
+    out[b * N2 + t] = (int16_t)r;
+  }
+}
+
 template <int N>
 __global__ void inverse_dct_u8_kernel(const float *__restrict__ coeffs, int height, int width,
                                       uint8_t *__restrict__ img, int64_t pitch) {
@@ -125,6 +162,22 @@ dctf_status dctf_forward_dct_f64(const uint8_t *image, int height, int width, in
   dctf_status st = check_image(image, height, width, pitch, n, coeffs);
   if (st != DCTF_OK) return st;
   cudaError_t e = launch_forward<double>(image, height, width, pitch, n, coeffs, stream);
+  return e == cudaSuccess ? DCTF_OK : cuda_error(e, "forward DCT launch");
+}
+
+dctf_status dctf_forward_dct_i16(const uint8_t *image, int height, int width, int64_t pitch,
+                                 int n, const uint16_t *q, int16_t *coeffs,
+                                 dctf_stream_t stream) {
+  dctf_status st = check_image(image, height, width, pitch, n, coeffs);
+  if (st != DCTF_OK) return st;
+  if (q == nullptr) return set_error(DCTF_EINVAL, "quantisation table is NULL");
+  const int64_t nblocks = (int64_t)(height / n) * (width / n);
+  switch (n) {
+    case 4: forward_dct_q16_kernel<4><<<(unsigned)((nblocks + 15) / 16), 256, 0, stream>>>(image, height, width, pitch, q, coeffs); break;
+    case 8: forward_dct_q16_kernel<8><<<(unsigned)((nblocks + 3) / 4), 256, 0, stream>>>(image, height, width, pitch, q, coeffs); break;
+    case 16: forward_dct_q16_kernel<16><<<(unsigned)nblocks, 256, 0, stream>>>(image, height, width, pitch, q, coeffs); break;
+  }
+  cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? DCTF_OK : cuda_error(e, "forward DCT launch");
 }
 

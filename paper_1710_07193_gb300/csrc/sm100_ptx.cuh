@@ -53,7 +53,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // when another role raised *abort (returns false) or after kWaitLimitNs: then
 // the first such event of the launch is recorded in *err as `code` and
 // *abort is raised so every role leaves its loop.
-__device__ __noinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort,
+static __device__ __noinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort,
                                           uint32_t *err, uint32_t code) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
@@ -79,7 +79,7 @@ __device__ __forceinline__ bool warp_wait_bounded(uint64_t *bar, uint32_t parity
 
 // Wait that ignores the abort flag (used to drain copies / MMAs already in
 // flight before the CTA exits); still bounded.
-__device__ __noinline__ bool wait_drain(uint64_t *bar, uint32_t parity, uint32_t *err,
+static __device__ __noinline__ bool wait_drain(uint64_t *bar, uint32_t parity, uint32_t *err,
                                         uint32_t code) {
   const uint64_t t0 = globaltimer();
   for (uint32_t i = 0;; ++i) {
@@ -108,6 +108,16 @@ __device__ __forceinline__ void tma_store_2d(const void *map, const void *src, i
       "cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
           reinterpret_cast<uint64_t>(map)),
       "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+// Untiled bulk copy global -> shared, completion counted on `bar` (both
+// addresses 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ void bulk_commit() {
@@ -220,6 +230,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       "tcgen05.wait::ld.sync.aligned;"
       : DCTF_W16(v, 0), DCTF_W16(v, 16)
       : "r"(taddr)
+      : "memory");
+}
+
+// Two 32-column loads of this lane's row, one wait for both.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, uint32_t (&a)[32],
+                                            uint32_t (&b)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+      "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : DCTF_W16(a, 0), DCTF_W16(a, 16), DCTF_W16(b, 0), DCTF_W16(b, 16)
+      : "r"(ta), "r"(tb)
       : "memory");
 }
 

@@ -1,0 +1,169 @@
+"""GPU: the persistent grouped apply (many images, each with its own operator,
+one launch) against the oracle, and against one dctf_apply per image.
+
+Same bars as tests/test_gpu_apply.py: coefficients within 1e-3 of the FP64
+oracle, uint8 pixels equal outside the 1e-4 tie band; int16 requantised
+outputs equal outside the same band (in units of y / q)."""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+COEF_TOL = 1e-3
+BAND = 1e-4
+
+
+def make_items(dctf, jobs):
+    items, refs = [], []
+    for job in jobs:
+        blocks = oracle.image_to_blocks(job.image, 8)
+        x = oracle.dct2_blocks(blocks).astype(np.float32)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.full_like(xd, float("nan"))
+        op = dctf.build_operator(job.mask, job.anchor, 8, job.boundary)
+        items.append((op, xd, yd, x.shape[0]))
+        refs.append((job, blocks, x))
+    return items, refs
+
+
+def check_item(y, job, blocks, x):
+    y_ref = oracle.apply_M(oracle.build_M(job.mask, job.anchor, 8, job.boundary),
+                           x.astype(np.float64))
+    assert np.abs(y - y_ref).max() <= COEF_TOL
+    p_sp = oracle.spatial_filter_blocks(blocks, job.mask, job.anchor, job.boundary)
+    st = oracle.uint8_compare(p_sp, oracle.to_uint8(oracle.idct2_blocks(y, 8)), BAND)
+    assert st["mismatch"] == 0, st
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    return datagen.grouped_jobs(count=16, scale=0.2)
+
+
+def test_group_matches_oracle_and_single_applies(dctf, small_batch):
+    items, refs = make_items(dctf, small_batch)
+    g = dctf.group_create(items)
+    g.launch()
+    torch.cuda.synchronize()
+    assert g.status() == 0
+    for (op, xd, yd, nb), (job, blocks, x) in zip(items, refs):
+        y = yd.cpu().numpy().astype(np.float64)
+        check_item(y, job, blocks, x)
+        # one plain launch per image gives the same bits
+        y1 = torch.empty_like(xd)
+        dctf.apply(op, xd, nb, y1)
+        torch.cuda.synchronize()
+        assert np.array_equal(y1.cpu().numpy(), yd.cpu().numpy())
+
+
+def test_group_graph_replay_and_tune(dctf, small_batch):
+    items, refs = make_items(dctf, small_batch)
+    g = dctf.group_create(items)
+    g.tune(reps=2)
+    # the tuner's last candidate ran half the CTAs with 64-row tiles
+    torch.cuda.synchronize()
+    for (_, _, yd, _), (job, blocks, x) in zip(items, refs):
+        check_item(yd.cpu().numpy().astype(np.float64), job, blocks, x)
+    grid, rows = g.config()
+    assert grid >= 1 and rows in (64, 128)
+    for _, _, yd, _ in items:
+        yd.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            g.launch(stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for (_, _, yd, _), (job, blocks, x) in zip(items, refs):
+        check_item(yd.cpu().numpy().astype(np.float64), job, blocks, x)
+    assert g.status() == 0
+
+
+def test_group_edge_items(dctf):
+    """Empty items, a 1-block item, a ragged item, an in-place item, and the
+    64-row tile mode."""
+    img = datagen.synthetic_image(512, 264, datagen.rng(97, 0, 0))   # 2112 blocks
+    blocks = oracle.image_to_blocks(img, 8)
+    x = oracle.dct2_blocks(blocks).astype(np.float32)
+    w, a = datagen.headline_mask(), (1, 3)
+    op = dctf.build_operator(w, a, 8, dctf.REPLICATE)
+    y_ref = oracle.apply_M(oracle.build_M(w, a, 8, oracle.REPLICATE), x.astype(np.float64))
+    sizes = [0, 1, 63, 65, 128, 0, 1000, 129]
+    items, views = [], []
+    off = 0
+    xin = torch.from_numpy(x).cuda()
+    for nb in sizes:
+        xi = xin[off:off + nb].clone() if nb else xin[:1].clone()
+        yi = torch.full_like(xi, float("nan"))
+        items.append((op, xi, yi, nb))
+        views.append((off, nb, yi))
+        off += nb
+    # in place: the last item writes over its own input
+    xi = xin[:300].clone()
+    items.append((op, xi, xi, 300))
+    views.append((0, 300, xi))
+    g = dctf.group_create(items)
+    g.launch()
+    torch.cuda.synchronize()
+    for o, nb, yi in views:
+        if nb:
+            assert np.abs(yi.cpu().numpy().astype(np.float64) - y_ref[o:o + nb]).max() <= COEF_TOL
+    assert g.status() == 0
+    with pytest.raises(dctf.DctfError):
+        g.tune()                   # an in-place item: refused
+
+
+def test_group_rejects_bad_items(dctf):
+    op8 = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 8, dctf.ZERO)
+    op16 = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 16, dctf.ZERO)
+    buf = torch.zeros(64 * 10 + 4, device="cuda")
+    with pytest.raises(dctf.DctfError):
+        dctf.group_create([(op16, buf, buf, 2)])
+    with pytest.raises(dctf.DctfError):
+        dctf.group_create([(op8, buf.data_ptr() + 4, buf.data_ptr() + 4, 2)])
+    with pytest.raises(dctf.DctfError):
+        dctf.group_create([(op8, buf, buf.data_ptr() + 256, 2)])
+    with pytest.raises(dctf.DctfError):
+        dctf.group_create([(op8, buf, buf, 2)], io=dctf.IO_I16)     # no q tables
+
+
+def quantised_plane(img, s):
+    q = datagen.quant_table(s)
+    x = oracle.dct2_blocks(oracle.image_to_blocks(img, 8))
+    qin = np.clip(oracle.round_half_away(x / q.ravel()[None, :].astype(np.float64)),
+                  -32768, 32767).astype(np.int16)
+    return qin, q
+
+
+def test_group_int16_dequant_requant(dctf):
+    """JPEG-style int16 planes, each with its own mask and quantisation
+    table: dequantise, filter, requantise in one pass."""
+    planes = []
+    for j in range(6):
+        img = datagen.synthetic_image(128 + 64 * (j % 3), 192, datagen.rng(98, j, 0))
+        s = [1, 2, 4][j % 3]
+        w, a, bnd = datagen.serving_mask(j)
+        planes.append((img, s, w, a, bnd))
+    items, refs, keep = [], [], []
+    for img, s, w, a, bnd in planes:
+        qin, q = quantised_plane(img, s)
+        op = dctf.build_operator(w, a, 8, bnd)
+        xd = torch.from_numpy(qin).cuda()
+        yd = torch.zeros_like(xd)
+        qd = torch.from_numpy(q.ravel().astype(np.int16).view(np.int16)).cuda()
+        keep.append(qd)
+        items.append((op, xd, yd, qin.shape[0], qd, qd))
+        refs.append((qin, q, w, a, bnd))
+    g = dctf.group_create(items, io=dctf.IO_I16)
+    g.launch()
+    torch.cuda.synchronize()
+    assert g.status() == 0
+    for (op, xd, yd, nb, _, _), (qin, q, w, a, bnd) in zip(items, refs):
+        out_ref, v = oracle.serve_blocks(qin, q, oracle.build_M(w, a, 8, bnd), q)
+        st = oracle.int16_compare(v, yd.cpu().numpy(), BAND)
+        assert st["mismatch"] == 0, st

@@ -1,0 +1,121 @@
+"""GPU: the continuous-batching server (int16 quantised planes).
+
+* each request's result is bit-identical whether it runs alone or in a
+  mixed burst (continuous batching must not change results), and equal to
+  the oracle's requantised output outside the 1e-4 tie band;
+* admission by HBM budget (a request that can never fit is refused),
+  operator cache hits / eviction, bounded waits, and an injected operator
+  build failure that fails only its own request while the server carries on.
+"""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+BAND = 1e-4
+
+
+def quantised(img, s):
+    q = datagen.quant_table(s)
+    x = oracle.dct2_blocks(oracle.image_to_blocks(img, 8))
+    qin = np.clip(oracle.round_half_away(x / q.ravel()[None, :].astype(np.float64)),
+                  -32768, 32767).astype(np.int16)
+    return qin, q.ravel()
+
+
+@pytest.fixture(scope="module")
+def requests():
+    """A small stream: scaled-down 4:2:0 frames (3 planes) and stills (1 plane)."""
+    out = []
+    for r in datagen.serving_stream(10, 2000.0, scale=0.15):
+        planes = [quantised(img, s) for img, s in zip(r.planes, r.q_scale)]
+        w, a, bnd = datagen.serving_mask(r.mask_id)
+        out.append((planes, w, a, bnd))
+    return out
+
+
+def run_one(srv, req):
+    planes, w, a, bnd = req
+    outs = [np.zeros_like(p[0]) for p in planes]
+    t = srv.submit([p[0] for p in planes], outs, [p[1] for p in planes], w, a, bnd)
+    return t, outs
+
+
+def test_alone_equals_mixed_and_oracle(dctf, requests):
+    srv = dctf.Server(hbm_budget_bytes=64 << 20, max_inflight=3, max_batch_requests=4)
+    alone = []
+    for req in requests:
+        t, outs = run_one(srv, req)
+        srv.wait(t)
+        alone.append(outs)
+    burst = [run_one(srv, req) for req in requests]
+    for t, _ in burst:
+        srv.wait(t)
+    for (planes, w, a, bnd), outs_alone, (_, outs_mix) in zip(requests, alone, burst):
+        m = oracle.build_M(w, a, 8, bnd)
+        for (qin, q), ya, ym in zip(planes, outs_alone, outs_mix):
+            assert np.array_equal(ya, ym)
+            _, v = oracle.serve_blocks(qin, q, m, q)
+            st = oracle.int16_compare(v, ya, BAND)
+            assert st["mismatch"] == 0, st
+    st = srv.stats()
+    assert st["completed"] == 2 * len(requests) and st["failed"] == 0
+    assert st["cache_hits"] > 0 and 0 < st["p50_ms"] <= st["p99_ms"]
+    assert st["max_batch_requests_seen"] > 1          # the burst really batched
+    assert st["hbm_in_use"] == 0
+    srv.close()
+
+
+def test_budget_cache_and_timeouts(dctf, requests):
+    srv = dctf.Server(hbm_budget_bytes=2 << 20, max_inflight=2, max_batch_requests=2,
+                      op_cache_capacity=2)
+    big = np.zeros((40000, 64), dtype=np.int16)           # 2 x 5 MB > 2 MB budget
+    with pytest.raises(dctf.DctfError) as e:
+        srv.submit([big], [np.zeros_like(big)], [datagen.quant_table(1)],
+                   datagen.gaussian_mask(3, 1.0), (1, 1), 0)
+    assert e.value.status == 4                            # EBUDGET
+    with pytest.raises(dctf.DctfError):
+        srv.wait(123456)                                  # unknown ticket
+    # stills only (fit the small budget), more distinct masks than the cache holds
+    stills = [r for r in requests if len(r[0]) == 1]
+    tickets = []
+    for j, (planes, _, _, _) in enumerate(stills * 2):
+        w, a, bnd = datagen.serving_mask(j % 5)
+        outs = [np.zeros_like(planes[0][0])]
+        tickets.append((srv.submit([planes[0][0]], outs, [planes[0][1]], w, a, bnd),
+                        outs, planes[0], (w, a, bnd)))
+    for t, outs, (qin, q), (w, a, bnd) in tickets:
+        try:
+            srv.wait(t, 0)                                # may still be running
+        except dctf.DctfError as err:
+            assert err.status == 5                        # ETIMEOUT: ticket stays valid
+            srv.wait(t)
+        _, v = oracle.serve_blocks(qin, q, oracle.build_M(w, a, 8, bnd), q)
+        assert oracle.int16_compare(v, outs[0], BAND)["mismatch"] == 0
+    st = srv.stats()
+    assert st["failed"] == 0 and st["cache_misses"] >= 5
+    srv.close()
+
+
+def test_injected_build_failure(dctf, requests):
+    srv = dctf.Server(hbm_budget_bytes=64 << 20, max_inflight=2, max_batch_requests=2,
+                      op_cache_capacity=1, inject_build_failure_every=2)
+    results = []
+    for j in range(6):
+        planes, _, _, _ = requests[j % len(requests)]
+        w, a, bnd = datagen.serving_mask(j)                 # a new operator every time
+        outs = [np.zeros_like(p[0]) for p in planes]
+        t = srv.submit([p[0] for p in planes], outs, [p[1] for p in planes], w, a, bnd)
+        try:
+            srv.wait(t)
+            results.append("ok")
+        except dctf.DctfError as err:
+            assert err.status == 3                        # the injected ECUDA
+            results.append("fail")
+    assert results.count("fail") == 3 and results.count("ok") == 3
+    st = srv.stats()
+    assert st["failed"] == 3 and st["completed"] == 3
+    srv.close()
