@@ -38,11 +38,14 @@ METRIC = "filtered 8x8 blocks/s, % HBM peak (TC-split vs FP32, uint8-exact); p99
 UNIT = "blocks/s"
 WORKLOAD = "4096x4096 uint8 image, 262144 8x8 blocks, FP32 coefficients, random asymmetric 5x5 mask anchor (1,3), border replication"
 BYTES_PER_BLOCK = 512          # 256 B of FP32 coefficients in + 256 B out
+FLOPS_PER_BLOCK_FP32 = 2 * 64 * 64   # one 64 x 64 matrix-vector product
 ROTATE = 8
 
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
-NCU_TRAFFIC = {}               # {sha1 of apply_group.cu: bytes per launch}
+NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
+    "0681e5cf44b3e55699e94710c1d423c057245e32": 132014438,
+}
 
 
 def parse():
@@ -57,6 +60,8 @@ def parse():
     p.add_argument("--no-simt", action="store_true", help="skip the FP32 CUDA-core comparison")
     p.add_argument("--no-serving", action="store_true", help="skip the serving (p50/p99) phase")
     p.add_argument("--serving-requests", type=int, default=400)
+    p.add_argument("--no-workloads", action="store_true",
+                   help="skip the small / grouped / 16x16 workloads")
     return p.parse_args()
 
 
@@ -255,6 +260,97 @@ def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
             "headline": max(ok, key=lambda r: r["rate_req_s"]) if ok else None}
 
 
+# ------------------------------------------------------------ other workloads
+def graph_time_ms(torch, fn, reps):
+    """Mean time of fn() over `reps` calls captured in one CUDA graph
+    (events around the replay)."""
+    fn(None)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        for _ in range(reps):
+            fn(s)
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_workloads(lib, torch, reps: int):
+    """The other four workloads, timed on the device (CUDA graphs)."""
+    dev = torch.device("cuda")
+    out = {}
+    # small: 256x256, 3x3 Gaussian sigma=1, zero padding, FP64 coefficients in
+    job = datagen.small_job()
+    img = torch.from_numpy(job.image).to(dev)
+    nb = 32 * 32
+    x64 = torch.empty((nb, 64), dtype=torch.float64, device=dev)
+    lib.forward_dct(img, 256, 256, 8, x64, f64=True)
+    x32 = x64.float()
+    y = torch.empty((nb, 64), dtype=torch.float32, device=dev)
+    op = lib.build_operator(job.mask, job.anchor, 8, job.boundary)
+    op.set_precision(lib.FP32_SIMT)
+    t64 = graph_time_ms(torch, lambda s: lib.apply_f64in(op, x64, nb, y, stream=s), reps)
+    op.set_precision(lib.F16X3)
+    t16 = graph_time_ms(torch, lambda s: lib.apply(op, x32, nb, y, stream=s), reps)
+    tb = graph_time_ms(torch, lambda s: op.rebuild(job.mask, job.anchor, job.boundary, stream=s), reps)
+    out["small_256x256"] = {"blocks": nb, "fp64_in_us": 1e3 * t64, "f16x3_fp32_in_us": 1e3 * t16,
+                            "operator_build_us": 1e3 * tb}
+    op.release()
+    # grouped: 64 images of seeded sizes, one mask and boundary each
+    jobs = datagen.grouped_jobs()
+    items, keep, nb_total = [], [], 0
+    for j in jobs:
+        h, w = j.image.shape
+        n = (h // 8) * (w // 8)
+        im = torch.from_numpy(j.image).to(dev)
+        xi = torch.empty((n, 64), dtype=torch.float32, device=dev)
+        lib.forward_dct(im, h, w, 8, xi)
+        yi = torch.empty_like(xi)
+        o = lib.build_operator(j.mask, j.anchor, 8, j.boundary)
+        items.append((o, xi, yi, n))
+        nb_total += n
+    grp = lib.group_create(items)
+    grp.tune(reps=5)
+    tg = graph_time_ms(torch, lambda s: grp.launch(stream=s), reps)
+    ts = graph_time_ms(torch, lambda s: [lib.apply(o, xi, n, yi, stream=s) for o, xi, yi, n in items],
+                       max(1, reps // 4))
+    grid, rows = grp.config()
+    out["grouped_64_images"] = {"blocks": nb_total, "one_launch_us": 1e3 * tg,
+                                "separate_launches_us": 1e3 * ts,
+                                "one_launch_blocks_per_s": nb_total / (tg / 1e3),
+                                "separate_blocks_per_s": nb_total / (ts / 1e3),
+                                "autotuned": {"ctas": grid, "tile_rows": rows},
+                                "one_launch_GBps": nb_total * BYTES_PER_BLOCK / (tg / 1e3) / 1e9}
+    grp.destroy()
+    for o, *_ in items:
+        o.release()
+    del items
+    # large: 8192x8192, 16x16 blocks, perturbed 9x9 Gaussian, replication
+    job = datagen.large_job()
+    img = torch.from_numpy(job.image).to(dev)
+    nb = (8192 // 16) ** 2
+    xl = torch.empty((nb, 256), dtype=torch.float32, device=dev)
+    lib.forward_dct(img, 8192, 8192, 16, xl)
+    del img
+    yl = torch.empty_like(xl)
+    op = lib.build_operator(job.mask, job.anchor, 16, job.boundary)
+    res = {"blocks": nb}
+    for name, prec in (("F16X3", lib.F16X3), ("FP32_SIMT", lib.FP32_SIMT)):
+        op.set_precision(prec)
+        t = graph_time_ms(torch, lambda s: lib.apply(op, xl, nb, yl, stream=s), max(1, reps // 4))
+        res[name] = {"us": 1e3 * t, "blocks_per_s": nb / (t / 1e3),
+                     "GBps": nb * 2048 / (t / 1e3) / 1e9}
+    out["large_8192x8192_16x16"] = res
+    op.release()
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_dctf(args):
     import torch
@@ -368,9 +464,15 @@ def run_dctf(args):
     simt = None
     if not args.no_simt:
         s_total, s_mean, _ = timed(lib.FP32_SIMT, args.steps, args.warmup)
+        # FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s
+        alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        alu = FLOPS_PER_BLOCK_FP32 * nb / (s_mean / 1e3) / 1e12
         simt = {"value": ws * nb * args.steps / (s_total / 1e3), "ms_per_step": s_total / args.steps,
                 "apply_us": 1e3 * s_mean,
-                "apply_GBps": BYTES_PER_BLOCK * nb / (s_mean / 1e3) / 1e9}
+                "apply_GBps": BYTES_PER_BLOCK * nb / (s_mean / 1e3) / 1e9,
+                "roofline": {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+                             "frac": alu / alu_peak,
+                             "peak_kind": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max clock"}}
     op = ops[0]
     op.set_precision(lib.F16X3)
     # the operator build alone (2 kernels), for the record
@@ -405,6 +507,9 @@ def run_dctf(args):
     serving = None
     if rank == 0 and not args.no_serving:
         serving = run_serving(lib, torch, args.serving_requests)
+    workloads = None
+    if rank == 0 and not args.no_workloads:
+        workloads = run_workloads(lib, torch, 40)
 
     status = ops[0].status() | ops[1].status()
     peak, peak_kind = measured_peaks()
@@ -433,6 +538,7 @@ def run_dctf(args):
         "fp32_simt": simt,
         "e2e": e2e,
         "serving": serving,
+        "workloads": workloads,
         "clocks": clocks,
         "device_status": status,
     }

@@ -66,6 +66,7 @@ typedef enum { DCTF_ZERO = 0, DCTF_REPLICATE = 1 } dctf_boundary;
  *  FP32_SIMT : plain FP32 FMA on CUDA cores (comparison kernel).
  *  F16X3     : tcgen05 tensor cores, FP16 hi/lo split of x and M,
  *              hi*hi + hi*lo + lo*hi.  |x| must stay below 65504.
+ *              n = 8 and n = 16 (16x16: not in place).
  *  TF32X3    : tcgen05, TF32 hi/lo split, three products (not yet built).
  *  BF16X6    : tcgen05, three BF16 pieces, six products (not yet built). */
 typedef enum {
@@ -121,8 +122,8 @@ dctf_status dctf_operator_status(dctf_operator *op, uint32_t *code, int clear);
 void dctf_release_operator(dctf_operator *op);
 
 /* y_b = M x_b for b < nblocks (Eq. 11 zero padding, Eq. 20 replication).
- *  coeffs, out  device [nblocks][n2] FP32; out == coeffs (in place) allowed,
- *               any other overlap is not.
+ *  coeffs, out  device [nblocks][n2] FP32; out == coeffs (in place) allowed
+ *               except for 16x16 blocks with DCTF_F16X3; no other overlap.
  * Arithmetic per dctf_operator_set_precision. */
 dctf_status dctf_apply(const dctf_operator *op, const float *coeffs,
                        int64_t nblocks, float *out, dctf_stream_t stream);

@@ -218,6 +218,11 @@ dctf_status dctf_apply(const dctf_operator *op, const float *coeffs, int64_t nbl
   cudaError_t e;
   if (op->precision == DCTF_FP32_SIMT) {
     e = launch_apply_simt(op, coeffs, nullptr, nblocks, out, stream);
+  } else if (op->n == 16) {
+    if (static_cast<const void *>(coeffs) == static_cast<const void *>(out))
+      return set_error(DCTF_EINVAL,
+                       "16x16 tensor-core apply cannot run in place (use DCTF_FP32_SIMT)");
+    e = launch_apply_n16(op, coeffs, nblocks, out, stream);
   } else {
     // one item of the persistent tensor-core kernel, descriptor by value
     GroupItem gi;

@@ -83,8 +83,13 @@ cudaError_t launch_apply_simt(const dctf_operator *op, const float *x,
                               const double *x64, int64_t nblocks, float *y,
                               cudaStream_t s);
 
-// apply_group.cu: tensor-core kernels exist for these (n, precision)
-inline bool tc_supported(int n, dctf_precision p) { return n == 8 && p == DCTF_F16X3; }
+// tensor-core kernels exist for these (n, precision): apply_group.cu (n = 8)
+// and apply_n16.cu (n = 16)
+inline bool tc_supported(int n, dctf_precision p) {
+  return (n == 8 || n == 16) && p == DCTF_F16X3;
+}
+cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks,
+                             float *y, cudaStream_t s);
 
 int sm_count(int device);
 

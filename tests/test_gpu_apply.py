@@ -46,7 +46,7 @@ def check(y, x32, blocks, w, a, n, boundary, pixels=True):
 
 
 def precisions(n, dctf):
-    return [dctf.FP32_SIMT, dctf.F16X3] if n == 8 else [dctf.FP32_SIMT]
+    return [dctf.FP32_SIMT, dctf.F16X3] if n in (8, 16) else [dctf.FP32_SIMT]
 
 
 @pytest.fixture(scope="module")
@@ -139,8 +139,13 @@ def test_other_block_sizes(dctf, n):
         op = dctf.build_operator(w, a, n, boundary)
         for p in precisions(n, dctf):
             check(run(dctf, op, x, p), x, blocks, w, a, n, boundary)
-        with pytest.raises(dctf.DctfError):
+        if n == 4:
+            with pytest.raises(dctf.DctfError):
+                op.set_precision(dctf.F16X3)
+        else:
             op.set_precision(dctf.F16X3)
+            with pytest.raises(dctf.DctfError):
+                run(dctf, op, x, dctf.F16X3, inplace=True)
 
 
 @pytest.mark.parametrize("prec", ["simt", "f16x3"])
@@ -218,3 +223,33 @@ def test_full_size_headline_sampled(dctf, headline_full):
         check(y[idx], x[idx], blocks[idx], job.mask, job.anchor, 8, job.boundary)
     assert np.abs(y_tc - y_simt).max() <= 2 * COEF_TOL
     assert op.status() == 0
+
+
+@pytest.mark.parametrize("nb", [1, 127, 129, 1000, 40000])
+def test_n16_tensor_core_ragged(dctf, nb):
+    """16x16 blocks, perturbed 9x9 Gaussian, border replication: the
+    tensor-core kernel (output halves on CTA pairs, K-chunked input)."""
+    img = datagen.synthetic_image(3200, 3200, datagen.rng(96, 0, 0))
+    blocks, x = coeffs_of(img, 16)
+    x = x[:nb].astype(np.float32)
+    blocks = blocks[:nb]
+    w, a = datagen.large_mask(), (4, 4)
+    op = dctf.build_operator(w, a, 16, dctf.REPLICATE)
+    check(run(dctf, op, x, dctf.F16X3), x, blocks, w, a, 16, oracle.REPLICATE)
+    assert op.status() == 0
+
+
+def test_error_table_16x16(dctf, capsys):
+    """Max coefficient error vs the FP64 oracle for each arithmetic on the
+    16x16 workload's mask (perturbed 9x9 Gaussian, border replication),
+    printed for the record; both stay within the bar."""
+    img = datagen.synthetic_image(2048, 2048, datagen.rng(datagen.W_LARGE, 0, 0))
+    blocks, x = coeffs_of(img, 16)
+    x = x.astype(np.float32)
+    w, a = datagen.large_mask(), (4, 4)
+    op = dctf.build_operator(w, a, 16, dctf.REPLICATE)
+    errs = {}
+    for name, p in (("FP32_SIMT", dctf.FP32_SIMT), ("F16X3", dctf.F16X3)):
+        errs[name] = check(run(dctf, op, x, p), x, blocks, w, a, 16, oracle.REPLICATE)
+    with capsys.disabled():
+        print(f"\n16x16 max coefficient error: {errs}")
