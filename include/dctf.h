@@ -308,6 +308,17 @@ dctf_status dctf_build_matrix_noalloc(const double *mask, int mh, int mw,
                                       dctf_boundary boundary, double *M_out,
                                       double *H_out, dctf_stream_t stream);
 
+/* Self-test of the device-side failure handling the tensor-core kernels
+ * use (no counterpart in the paper): one CTA waits, with a bound of
+ * limit_us microseconds (1..100000), on a barrier nothing ever completes.
+ * The waiting role must give up, record its code (0x101) and raise the
+ * CTA's abort flag; a second role waiting elsewhere must leave through that
+ * flag (other_role_aborted = 1).  The kernel returns normally: nothing
+ * faults or hangs.  Synchronous; returns DCTF_ETIMEOUT when the timeout was
+ * detected as designed. */
+dctf_status dctf_selftest_wait_timeout(uint32_t limit_us, uint32_t *code,
+                                       uint32_t *other_role_aborted);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *dctf_last_error(void);
 

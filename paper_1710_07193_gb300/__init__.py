@@ -54,6 +54,7 @@ _SIGS = {
     "dctf_group_status": (_i32, [_vp, _vp, _i32]),
     "dctf_group_destroy": (None, [_vp]),
     "dctf_apply_grouped": (_i32, [_vp, _i32, _i32, _vp]),
+    "dctf_selftest_wait_timeout": (_i32, [_u32, _vp, _vp]),
     "dctf_last_error": (ctypes.c_char_p, []),
     "dctf_version": (_i32, []),
 }
@@ -202,6 +203,13 @@ def inverse_dct_u8(coeffs, height: int, width: int, n: int, image, pitch: int | 
     """Device FP32 coefficients -> uint8 image (rounded half away, saturated)."""
     _check(load().dctf_inverse_dct_u8(_ptr(coeffs), height, width, n, _ptr(image),
                                       pitch or width, _stream(stream)))
+
+
+def selftest_wait_timeout(limit_us: int = 2000) -> tuple[int, int, int]:
+    """Run the bounded-wait self-test; returns (status, code, other_role_aborted)."""
+    code, other = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    st = load().dctf_selftest_wait_timeout(limit_us, ctypes.addressof(code), ctypes.addressof(other))
+    return st, code.value, other.value
 
 
 def apply_host(op: Operator, host_in, nblocks: int, host_out) -> None:

@@ -53,19 +53,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // when another role raised *abort (returns false) or after kWaitLimitNs: then
 // the first such event of the launch is recorded in *err as `code` and
 // *abort is raised so every role leaves its loop.
-static __device__ __noinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort,
-                                          uint32_t *err, uint32_t code) {
+static __device__ __noinline__ bool wait_bounded_ns(uint64_t *bar, uint32_t parity,
+                                                    volatile int *abort, uint32_t *err,
+                                                    uint32_t code, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if ((i & 255) == 0 && globaltimer() - t0 > kWaitLimitNs) {
+    if ((i & 255) == 0 && globaltimer() - t0 > limit_ns) {
       atomicCAS(err, 0u, code);
       *abort = 1;
       return false;
     }
   }
+}
+static __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity,
+                                                    volatile int *abort, uint32_t *err,
+                                                    uint32_t code) {
+  return wait_bounded_ns(bar, parity, abort, err, code, kWaitLimitNs);
 }
 
 // Warp-collective form: every lane polls, and the warp leaves together (all
