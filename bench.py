@@ -193,7 +193,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ serving
-SERVING_RATES = (500.0, 1000.0, 2000.0)
+SERVING_RATES = (1000.0, 2000.0, 5000.0, 10000.0)
 
 
 def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
@@ -213,7 +213,8 @@ def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
                     q = torch.from_numpy(datagen.quant_table(sc).ravel().astype(np.int16)).to(dev)
                     out = torch.empty(((h // 8) * (w // 8), 64), dtype=torch.int16, device=dev)
                     lib.forward_dct_i16(img, h, w, 8, q, out)
-                    pool[(kind, v, p, sc)] = out.cpu().numpy()
+                    pinned = out.cpu().pin_memory()        # page-locked: the server DMAs it
+                    pool[(kind, v, p, sc)] = (pinned, pinned.numpy())
     qtabs = {sc: datagen.quant_table(sc).ravel() for sc in (1, 2, 4)}
     masks = [datagen.serving_mask(j) for j in range(32)]
     results = []
@@ -233,12 +234,13 @@ def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
             while time.perf_counter() < target:
                 pass
             v = i % 2
-            ins = [pool[(r.kind, v, p, sc)] for p, sc in enumerate(r.q_scale)]
-            if outs[i % ring] is None or len(outs[i % ring]) != len(ins) or any(
-                    o.shape != x.shape for o, x in zip(outs[i % ring], ins)):
-                outs[i % ring] = [np.empty_like(x) for x in ins]
+            ins = [pool[(r.kind, v, p, sc)][1] for p, sc in enumerate(r.q_scale)]
+            if outs[i % ring] is None or len(outs[i % ring][1]) != len(ins) or any(
+                    o.shape != x.shape for o, x in zip(outs[i % ring][1], ins)):
+                tens = [torch.empty(x.shape, dtype=torch.int16).pin_memory() for x in ins]
+                outs[i % ring] = (tens, [t.numpy() for t in tens])
             w, a, bnd = masks[r.mask_id]
-            tickets.append(srv.submit(ins, outs[i % ring], [qtabs[sc] for sc in r.q_scale],
+            tickets.append(srv.submit(ins, outs[i % ring][1], [qtabs[sc] for sc in r.q_scale],
                                       w, a, bnd))
         for t in tickets[max(0, len(tickets) - ring):]:
             srv.wait(t)
@@ -255,7 +257,8 @@ def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
                         "failed": st["failed"]})
     ok = [r for r in results if r["p99_ms"] < 10.0]
     return {"stream": "Poisson; 50% 1920x1088 4:2:0 frames, 50% 512x512 stills; int16, "
-                      "q[u,v]=1+round(s(1+u+v)), s in {1,2,4}; 32 seeded masks 3x3..7x7",
+                      "q[u,v]=1+round(s(1+u+v)), s in {1,2,4}; 32 seeded masks 3x3..7x7; "
+                      "page-locked host buffers",
             "rates": results,
             "headline": max(ok, key=lambda r: r["rate_req_s"]) if ok else None}
 
@@ -380,6 +383,8 @@ def run_dctf(args):
     # two operators: step i applies ops[i % 2] while the side stream rebuilds
     # the other one for step i + 1 (each step still builds its own operator)
     ops = [lib.build_operator(job.mask, job.anchor, 8, job.boundary) for _ in range(2)]
+    for op in ops:   # the inputs are resident before the timed region
+        op.set_flags(lib.APPLY_INPUTS_READY)
     torch.cuda.synchronize()
 
     def loop_graph(steps, prec):
@@ -502,7 +507,7 @@ def run_dctf(args):
     e_dt = time.perf_counter() - e0
     e2e = {"value": ws * nb * e2e_steps / e_dt, "unit": UNIT,
            "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
-           "steps": e2e_steps, "path": "dctf_apply_host, pinned host buffers, 64k-block chunks on 2 streams"}
+           "steps": e2e_steps, "path": "dctf_apply_host, pinned host buffers, 4 MB chunks on 4 streams"}
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -524,7 +529,8 @@ def run_dctf(args):
         "config": {"workload": WORKLOAD, "blocks_per_step": nb, "precision": "F16X3",
                    "step": "operator rebuild (FP64, 2 kernels) + apply (1 kernel); "
                            "build of step i+1 overlaps apply of step i (two operators)",
-                   "submission": "one CUDA graph per timed loop",
+                   "submission": "one CUDA graph per timed loop; applies launched with "
+                                 "DCTF_APPLY_INPUTS_READY (programmatic dependent launch)",
                    "build_us": build_us,
                    "l2": f"{ROTATE} rotating input/output buffer pairs, "
                          f"{ROTATE * 2 * nb * 256 / 1e9:.2f} GB > L2",

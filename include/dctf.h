@@ -93,6 +93,16 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw,
                                 dctf_boundary boundary, dctf_stream_t stream,
                                 dctf_operator **out);
 
+/* As dctf_build_operator, with flags.  DCTF_MASK_CONVOLUTION applies the
+ * mask as a convolution, out(i,j) = sum_{r,c} w[r][c] x(i-r+ar, j-c+ac)
+ * (the other natural reading of Eq. 5), i.e. a correlation with the mask
+ * rotated by 180 degrees and the anchor mirrored to (mh-1-ar, mw-1-ac). */
+enum { DCTF_MASK_CONVOLUTION = 1u };
+dctf_status dctf_build_operator_ex(const double *mask, int mh, int mw,
+                                   const int anchor[2], int n,
+                                   dctf_boundary boundary, uint32_t flags,
+                                   dctf_stream_t stream, dctf_operator **out);
+
 /* Rebuild an existing operator for a new mask of the same n, in place, on
  * `stream` (the paper's point that the prepared matrices are simply rebuilt
  * when the mask changes, Sec. I and IV).  Allocates nothing; the mask travels
@@ -106,6 +116,19 @@ dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask,
 /* Choose the arithmetic of later dctf_apply calls.  EUNSUPPORTED if no
  * kernel exists for (n, p).  Not synchronised with concurrent applies. */
 dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p);
+
+/* Flags for dctf_operator_set_flags.
+ * DCTF_APPLY_INPUTS_READY: the caller guarantees that the input of every
+ *   dctf_apply through this operator is already in place when the apply is
+ *   queued (not written by the kernel queued just before it on the stream).
+ *   The 8x8 tensor-core apply is then launched with programmatic stream
+ *   serialisation: its CTAs start on SMs the previous kernel has left and
+ *   begin reading while that kernel finishes.  No output is written before
+ *   the previous kernel has completed.  Ignored by the other kernels. */
+enum { DCTF_APPLY_INPUTS_READY = 1u };
+
+/* Set the DCTF_APPLY_* flags of later dctf_apply calls (0 clears them). */
+dctf_status dctf_operator_set_flags(dctf_operator *op, uint32_t flags);
 
 /* Read back (synchronously, after the build finished) the FP64 operator M
  * (n2*n2, row-major: row = output coefficient) and, if H_host is not NULL,
@@ -135,13 +158,13 @@ dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs,
                              dctf_stream_t stream);
 
 /* End-to-end call for callers holding the data in HOST memory: copies
- * host_in to the device, applies, copies the result to host_out, in chunks
- * pipelined over two internal streams and device buffers owned by the
- * operator.  The internal streams are blocking streams: the copies start
+ * host_in to the device, applies, copies the result to host_out, in 4 MB
+ * chunks pipelined over four internal streams and device buffers owned by
+ * the operator.  The internal streams are blocking streams: the copies start
  * after work already queued on the legacy default stream (e.g. a rebuild).
  * Synchronous: returns after host_out is written.  host_in and host_out
  * should be pinned (cudaHostAlloc) for full speed.  The first call allocates
- * the staging buffers (4 x 16 MB at n = 8). */
+ * the staging buffers (8 x 4 MB). */
 dctf_status dctf_apply_host(dctf_operator *op, const float *host_in,
                             int64_t nblocks, float *host_out);
 
@@ -248,7 +271,9 @@ typedef struct dctf_server dctf_server;
 dctf_status dctf_server_create(const dctf_server_cfg *cfg, dctf_server **out);
 
 /* Queue a request; its host buffers must stay valid until dctf_server_wait
- * returns for its ticket.  EBUDGET if it can never fit the HBM budget. */
+ * returns for its ticket.  Page-locked buffers (cudaHostAlloc or
+ * cudaHostRegister) are copied by DMA directly; others go through the
+ * server's pinned staging.  EBUDGET if it can never fit the HBM budget. */
 dctf_status dctf_server_submit(dctf_server *s, const dctf_request *req,
                                uint64_t *ticket);
 

@@ -22,6 +22,8 @@ __all__ = [
 
 ZERO, REPLICATE = 0, 1
 IO_F32, IO_I16 = 0, 1
+APPLY_INPUTS_READY = 1
+MASK_CONVOLUTION = 1
 FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3 = 0, 1, 2, 3, 4
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ETIMEOUT",
            6: "EUNSUPPORTED"}
@@ -34,8 +36,10 @@ _vp, _i32, _i64, _u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_
 # name -> (restype, argtypes); mirrors include/dctf.h
 _SIGS = {
     "dctf_build_operator": (_i32, [_vp, _i32, _i32, _vp, _i32, _i32, _vp, _vp]),
+    "dctf_build_operator_ex": (_i32, [_vp, _i32, _i32, _vp, _i32, _i32, _u32, _vp, _vp]),
     "dctf_operator_rebuild": (_i32, [_vp, _vp, _i32, _i32, _vp, _i32, _vp]),
     "dctf_operator_set_precision": (_i32, [_vp, _i32]),
+    "dctf_operator_set_flags": (_i32, [_vp, _u32]),
     "dctf_operator_download": (_i32, [_vp, _vp, _vp]),
     "dctf_operator_status": (_i32, [_vp, _vp, _i32]),
     "dctf_release_operator": (None, [_vp]),
@@ -141,6 +145,9 @@ class Operator:
     def set_precision(self, p: int) -> None:
         _check(load().dctf_operator_set_precision(self.handle, p))
 
+    def set_flags(self, flags: int) -> None:
+        _check(load().dctf_operator_set_flags(self.handle, flags))
+
     def download(self) -> tuple[np.ndarray, np.ndarray]:
         m = np.empty((self.n2, self.n2), dtype=np.float64)
         h = np.empty((self.n2, self.n2), dtype=np.float64)
@@ -164,14 +171,17 @@ class Operator:
             pass
 
 
-def build_operator(mask, anchor, n: int, boundary: int, stream=None) -> Operator:
+def build_operator(mask, anchor, n: int, boundary: int, stream=None,
+                   convolution: bool = False) -> Operator:
     m = np.ascontiguousarray(mask, dtype=np.float64)
     if m.ndim != 2:
         raise ValueError("mask must be 2-D")
     a = (ctypes.c_int * 2)(*anchor)
     h = ctypes.c_void_p(0)
-    _check(load().dctf_build_operator(m.ctypes.data, m.shape[0], m.shape[1], ctypes.addressof(a),
-                                      n, boundary, _stream(stream), ctypes.addressof(h)))
+    _check(load().dctf_build_operator_ex(m.ctypes.data, m.shape[0], m.shape[1],
+                                         ctypes.addressof(a), n, boundary,
+                                         MASK_CONVOLUTION if convolution else 0,
+                                         _stream(stream), ctypes.addressof(h)))
     return Operator(h.value, n)
 
 

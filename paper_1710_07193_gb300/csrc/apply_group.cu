@@ -245,6 +245,9 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  // A launch of this kernel that follows on the stream may be scheduled now
+  // (it only does so when launched for programmatic stream serialisation).
+  if (tid == 0) pdl_launch_dependents();
 
   TileWalk walk;
   walk.init(items, nitems, total_halves, max_take, interleaved != 0);
@@ -406,6 +409,11 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
     // ---------------------------------------------------------- epilogue
     const int row = tid - 256, wr = warp & 3, r32 = lane;
     const uint32_t lane_base = (uint32_t)(wr * 32) << 16;
+    // Under programmatic dependent launch the loads above may run while the
+    // previous kernel on the stream finishes; no output is written before
+    // that kernel has completed (it may still read the output buffer).
+    if (lane == 0) pdl_wait();
+    __syncwarp();
     int it = 0;
     while (walk.next(t)) {
       const int b = it % kBufs, o = it & 1, r = it % kDcRing, k = t.seg % NS;
@@ -537,13 +545,26 @@ cudaError_t make_map(CUtensorMap *m, const void *ptr, int64_t nblocks, bool i16,
 template <typename IoT, int S, int NS, bool kGroup>
 cudaError_t launch_cfg(const GroupItem *d_items, const GroupItem &single, int nitems,
                        int64_t total_halves, int grid, int max_take, int interleaved,
-                       uint32_t *err, cudaStream_t s) {
+                       uint32_t *err, cudaStream_t s, bool pdl) {
   auto kern = apply_group_kernel<IoT, S, NS, kGroup>;
   constexpr int smem = Layout<IoT, S, NS>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, smem, s>>>(d_items, single, nitems, total_halves, max_take, interleaved,
-                                    err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (pdl) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  e = cudaLaunchKernelEx(&cfg, kern, d_items, single, nitems, total_halves, max_take, interleaved,
+                         err);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -568,7 +589,7 @@ cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,
-                               uint32_t *err, cudaStream_t s) {
+                               uint32_t *err, cudaStream_t s, bool pdl) {
   if (total_halves <= 0) return cudaSuccess;
   int64_t g = grid > 0 ? grid : 0;
   if (g > total_halves) g = total_halves;
@@ -577,14 +598,14 @@ cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single
   const int take = max_take == 1 ? 1 : 2;
   if (single != nullptr) {   // one item: interleaved schedule, one operator slot, 4 stages
     return i16 ? launch_cfg<int16_t, 4, 1, false>(nullptr, *single, 1, total_halves, (int)g, take,
-                                                 1, err, s)
+                                                 1, err, s, pdl)
                : launch_cfg<float, 4, 1, false>(nullptr, *single, 1, total_halves, (int)g, take, 1,
-                                               err, s);
+                                               err, s, pdl);
   }
   return i16 ? launch_cfg<int16_t, 4, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take,
-                                              0, err, s)
+                                              0, err, s, pdl)
              : launch_cfg<float, 3, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take, 0,
-                                            err, s);
+                                            err, s, pdl);
 }
 
 }  // namespace dctf

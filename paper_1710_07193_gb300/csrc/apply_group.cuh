@@ -33,9 +33,10 @@ cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *
 
 // d_items: device array (group mode, single == nullptr) or single: one item
 // passed by value.  grid <= 0 means one CTA per SM.  max_take: 2 for 128-row
-// tiles, 1 for 64-row tiles.
+// tiles, 1 for 64-row tiles.  pdl: launch with programmatic stream
+// serialisation (the inputs must not be written by the preceding kernel).
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,
-                               uint32_t *err, cudaStream_t s);
+                               uint32_t *err, cudaStream_t s, bool pdl = false);
 
 }  // namespace dctf

@@ -136,6 +136,23 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   return DCTF_OK;
 }
 
+dctf_status dctf_build_operator_ex(const double *mask, int mh, int mw, const int anchor[2], int n,
+                                   dctf_boundary boundary, uint32_t flags, dctf_stream_t stream,
+                                   dctf_operator **out) {
+  if (flags & ~(uint32_t)DCTF_MASK_CONVOLUTION) return set_error(DCTF_EINVAL, "unknown flags");
+  if (!(flags & DCTF_MASK_CONVOLUTION))
+    return dctf_build_operator(mask, mh, mw, anchor, n, boundary, stream, out);
+  // convolution with w, anchor a = correlation with w rotated by 180 degrees
+  // and the anchor mirrored: (mh - 1 - ar, mw - 1 - ac)
+  if (mask == nullptr || anchor == nullptr || mh < 1 || mw < 1 || mh > kMaxN || mw > kMaxN)
+    return set_error(DCTF_EINVAL, "bad mask");
+  double rot[kMaxN2];
+  for (int r = 0; r < mh; ++r)
+    for (int c = 0; c < mw; ++c) rot[(mh - 1 - r) * mw + (mw - 1 - c)] = mask[r * mw + c];
+  const int a2[2] = {mh - 1 - anchor[0], mw - 1 - anchor[1]};
+  return dctf_build_operator(rot, mh, mw, a2, n, boundary, stream, out);
+}
+
 dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask, int mh, int mw,
                                   const int anchor[2], dctf_boundary boundary,
                                   dctf_stream_t stream) {
@@ -162,6 +179,13 @@ dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p) {
   return DCTF_OK;
 }
 
+dctf_status dctf_operator_set_flags(dctf_operator *op, uint32_t flags) {
+  if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
+  if (flags & ~(uint32_t)DCTF_APPLY_INPUTS_READY) return set_error(DCTF_EINVAL, "unknown flags");
+  op->flags = flags;
+  return DCTF_OK;
+}
+
 dctf_status dctf_operator_download(const dctf_operator *op, double *M_host, double *H_host) {
   if (op == nullptr || M_host == nullptr) return set_error(DCTF_EINVAL, "NULL argument");
   size_t bytes = (size_t)op->n2 * op->n2 * sizeof(double);
@@ -184,9 +208,8 @@ dctf_status dctf_operator_status(dctf_operator *op, uint32_t *code, int clear) {
 
 void dctf_release_operator(dctf_operator *op) {
   if (op == nullptr) return;
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < dctf_operator::kHostPipes; ++i) {
     if (op->host_streams[i]) cudaStreamDestroy(op->host_streams[i]);
-    if (op->host_events[i]) cudaEventDestroy(op->host_events[i]);
     for (int j = 0; j < 2; ++j)
       if (op->d_stage[i][j]) cudaFree(op->d_stage[i][j]);
   }
@@ -229,7 +252,7 @@ dctf_status dctf_apply(const dctf_operator *op, const float *coeffs, int64_t nbl
     e = fill_group_item(&gi, op, coeffs, out, nblocks, false, nullptr, nullptr);
     if (e == cudaSuccess)
       e = launch_apply_group(nullptr, &gi, 1, (nblocks + 63) / 64, false, sm_count(op->device), 2,
-                             op->d_err, stream);
+                             op->d_err, stream, (op->flags & DCTF_APPLY_INPUTS_READY) != 0);
   }
   if (e != cudaSuccess) return cuda_error(e, "dctf_apply launch");
   return DCTF_OK;
@@ -252,22 +275,23 @@ dctf_status dctf_apply_host(dctf_operator *op, const float *host_in, int64_t nbl
   if (nblocks < 0) return set_error(DCTF_EINVAL, "nblocks < 0");
   if (nblocks == 0) return DCTF_OK;
   if (host_in == nullptr || host_out == nullptr) return set_error(DCTF_EINVAL, "NULL buffer");
-  const int64_t chunk = 65536;
+  constexpr int P = dctf_operator::kHostPipes;
   const size_t row = (size_t)op->n2 * sizeof(float);
+  const int64_t chunk = (int64_t)((4u << 20) / row);    // 4 MB of coefficients per chunk
   if (op->d_stage[0][0] == nullptr) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < P; ++i) {
       for (int j = 0; j < 2; ++j) DCTF_CUDA(cudaMalloc(&op->d_stage[i][j], chunk * row));
       DCTF_CUDA(cudaStreamCreateWithFlags(&op->host_streams[i], cudaStreamDefault));
-      DCTF_CUDA(cudaEventCreateWithFlags(&op->host_events[i], cudaEventDisableTiming));
     }
     op->stage_blocks = chunk;
   }
-  // chunk c uses stream / buffers c % 2: its H2D overlaps chunk c-1's
-  // compute and D2H (separate copy engines per direction).
-  int64_t nchunks = (nblocks + chunk - 1) / chunk;
+  // chunk c runs on pipe c % P: its host->device copy, the apply and its
+  // device->host copy are ordered on that stream, and the P pipes overlap,
+  // so both copy engines and the SMs stay busy.
+  const int64_t nchunks = (nblocks + chunk - 1) / chunk;
   for (int64_t c = 0; c < nchunks; ++c) {
-    int k = (int)(c & 1);
-    int64_t b0 = c * chunk, nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
+    const int k = (int)(c % P);
+    const int64_t b0 = c * chunk, nb = nblocks - b0 < chunk ? nblocks - b0 : chunk;
     cudaStream_t s = op->host_streams[k];
     DCTF_CUDA(cudaMemcpyAsync(op->d_stage[k][0], host_in + b0 * op->n2, nb * row,
                               cudaMemcpyHostToDevice, s));
@@ -276,7 +300,7 @@ dctf_status dctf_apply_host(dctf_operator *op, const float *host_in, int64_t nbl
     DCTF_CUDA(cudaMemcpyAsync(host_out + b0 * op->n2, op->d_stage[k][1], nb * row,
                               cudaMemcpyDeviceToHost, s));
   }
-  for (int k = 0; k < 2; ++k) DCTF_CUDA(cudaStreamSynchronize(op->host_streams[k]));
+  for (int k = 0; k < P; ++k) DCTF_CUDA(cudaStreamSynchronize(op->host_streams[k]));
   return DCTF_OK;
 }
 

@@ -53,6 +53,7 @@ struct dctf_operator {
   int mh, mw, ar, ac;
   int boundary;
   dctf_precision precision;
+  uint32_t flags;           // DCTF_APPLY_* flags
   int f16_scale_exp;        // pieces hold M * 2^f16_scale_exp
   // one device allocation, carved:
   void *d_base;
@@ -65,11 +66,12 @@ struct dctf_operator {
   float *d_Mdc;             // [n2] M[:, 0] in FP32
   __half *d_f16;            // F16X3 pieces: rows 0..n2-1 hi, n2..2n2-1 lo (sw128)
   uint32_t *d_err;          // device status word
-  // dctf_apply_host staging (lazily allocated)
-  float *d_stage[2][2];
+  // dctf_apply_host staging (lazily allocated): kHostPipes streams, each
+  // with an input and an output chunk buffer
+  static constexpr int kHostPipes = 4;
+  float *d_stage[kHostPipes][2];
   size_t stage_blocks;
-  cudaStream_t host_streams[2];
-  cudaEvent_t host_events[2];
+  cudaStream_t host_streams[kHostPipes];
 };
 
 namespace dctf {

@@ -9,10 +9,11 @@
 //   * builds or reuses each request's operator: an LRU cache keyed by
 //     (mask, anchor, boundary, n), FP64 build on its own stream, an event
 //     marks it ready; operators used by an in-flight batch are never evicted;
-//   * launches the batch: pinned staging -> HBM copies, ONE persistent
-//     grouped kernel over all planes of all admitted requests (dequantise,
-//     filter, requantise fused), HBM -> pinned copies, all on the slot's
-//     stream.
+//   * launches the batch: host -> HBM copies (straight from the caller's
+//     buffers when they are page-locked, else through pinned staging), ONE
+//     persistent grouped kernel over all planes of all admitted requests
+//     (dequantise, filter, requantise fused), HBM -> host copies, all on the
+//     slot's stream.
 // Several slots are in flight at once on separate streams, so requests that
 // arrive while a batch runs are admitted as soon as a slot and memory free
 // up, and their copies and kernels overlap the running batch on the device.
@@ -134,7 +135,20 @@ struct Req {
   OpEntry *op = nullptr;
   dctf_status status = DCTF_OK;
   bool done = false;
+  bool in_pinned = false;    // caller buffers already page-locked: copied by DMA directly
+  bool out_pinned = false;
 };
+
+// Page-locked (or registered) host memory can be the source / target of an
+// asynchronous copy directly; anything else goes through the pinned staging.
+bool is_pinned(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -256,7 +270,7 @@ void retire(dctf_server *s) {
     const dctf_status kst =
         *sl.h_err == 0 ? DCTF_OK : set_error(DCTF_ETIMEOUT, "device wait timed out");
     for (Req *r : sl.reqs) {
-      if (r->status == DCTF_OK) {
+      if (r->status == DCTF_OK && !r->out_pinned) {
         for (int p = 0; p < r->nplanes; ++p)
           memcpy(r->out[p], s->h_arena + r->out_off[p], (size_t)r->nblocks[p] * 128);
       }
@@ -277,12 +291,21 @@ dctf_status launch_batch(dctf_server *s, Slot &sl, std::vector<Req *> &batch) {
   for (Req *r : batch) {
     r->status = get_op(s, r);
     if (r->status != DCTF_OK) continue;
-    for (int p = 0; p < r->nplanes; ++p) {
-      memcpy(s->h_arena + r->in_off[p], r->in[p], (size_t)r->nblocks[p] * 128);
-      memcpy(s->h_arena + r->q_off[p], r->q[p], 128);
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < r->nplanes; ++p) memcpy(s->h_arena + r->q_off[p], r->q[p], 128);
+    if (r->in_pinned) {
+      for (int p = 0; p < r->nplanes && e == cudaSuccess; ++p)
+        e = cudaMemcpyAsync(s->d_arena + r->in_off[p], r->in[p], (size_t)r->nblocks[p] * 128,
+                            cudaMemcpyHostToDevice, sl.stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_arena + r->q_off[0], s->h_arena + r->q_off[0],
+                            (size_t)r->nplanes * kAlign, cudaMemcpyHostToDevice, sl.stream);
+    } else {
+      for (int p = 0; p < r->nplanes; ++p)
+        memcpy(s->h_arena + r->in_off[p], r->in[p], (size_t)r->nblocks[p] * 128);
+      e = cudaMemcpyAsync(s->d_arena + r->off, s->h_arena + r->off, r->in_bytes,
+                          cudaMemcpyHostToDevice, sl.stream);
     }
-    cudaError_t e = cudaMemcpyAsync(s->d_arena + r->off, s->h_arena + r->off, r->in_bytes,
-                                    cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.stream, r->op->ready, 0);
     if (e != cudaSuccess) return cuda_error(e, "batch input copy");
     for (int p = 0; p < r->nplanes; ++p) {
@@ -306,8 +329,14 @@ dctf_status launch_batch(dctf_server *s, Slot &sl, std::vector<Req *> &batch) {
                              sl.stream);
     for (Req *r : batch) {
       if (e != cudaSuccess || r->status != DCTF_OK) continue;
-      e = cudaMemcpyAsync(s->h_arena + r->out_start, s->d_arena + r->out_start,
-                          r->bytes - (r->out_start - r->off), cudaMemcpyDeviceToHost, sl.stream);
+      if (r->out_pinned) {
+        for (int p = 0; p < r->nplanes && e == cudaSuccess; ++p)
+          e = cudaMemcpyAsync(r->out[p], s->d_arena + r->out_off[p], (size_t)r->nblocks[p] * 128,
+                              cudaMemcpyDeviceToHost, sl.stream);
+      } else {
+        e = cudaMemcpyAsync(s->h_arena + r->out_start, s->d_arena + r->out_start,
+                            r->bytes - (r->out_start - r->off), cudaMemcpyDeviceToHost, sl.stream);
+      }
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, sl.stream);
@@ -467,6 +496,11 @@ dctf_status dctf_server_submit(dctf_server *s, const dctf_request *rq, uint64_t 
   r->key.ar = rq->anchor[0]; r->key.ac = rq->anchor[1];
   r->key.boundary = rq->boundary;
   r->bytes = bytes;
+  r->in_pinned = r->out_pinned = true;
+  for (int p = 0; p < rq->nplanes; ++p) {
+    r->in_pinned = r->in_pinned && is_pinned(rq->in[p]);
+    r->out_pinned = r->out_pinned && is_pinned(rq->out[p]);
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) { delete r; return set_error(DCTF_EINVAL, "server is stopping"); }

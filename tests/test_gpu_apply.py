@@ -253,3 +253,42 @@ def test_error_table_16x16(dctf, capsys):
         errs[name] = check(run(dctf, op, x, p), x, blocks, w, a, 16, oracle.REPLICATE)
     with capsys.disabled():
         print(f"\n16x16 max coefficient error: {errs}")
+
+
+def test_inputs_ready_flag(dctf, ragged_source):
+    """DCTF_APPLY_INPUTS_READY (programmatic dependent launch): chained
+    applies give the same bits as ordinary launches, including when a launch
+    overwrites the buffer the previous launch is still reading."""
+    _, x = ragged_source
+    w, a = datagen.headline_mask(), (1, 3)
+    op = dctf.build_operator(w, a, 8, dctf.REPLICATE)
+    xs = [torch.from_numpy(x).cuda() for _ in range(3)]
+    ref = [torch.empty_like(xs[0]) for _ in range(3)]
+    for i in range(3):
+        dctf.apply(op, xs[i], x.shape[0], ref[i])
+    torch.cuda.synchronize()
+    op.set_flags(dctf.APPLY_INPUTS_READY)
+    outs = [torch.full_like(xs[0], float("nan")) for _ in range(3)]
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        dctf.apply(op, xs[0], x.shape[0], outs[0], stream=s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            for i in range(3):
+                dctf.apply(op, xs[i], x.shape[0], outs[i], stream=s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for i in range(3):
+        assert torch.equal(outs[i], ref[i])
+    # write-after-read: the second launch writes the first launch's input
+    src = torch.from_numpy(x).cuda()
+    y = torch.empty_like(src)
+    other = torch.from_numpy(x[::-1].copy()).cuda()
+    dctf.apply(op, src, x.shape[0], y)
+    dctf.apply(op, other, x.shape[0], src)
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref[0])
+    op.set_flags(0)
+    assert op.status() == 0

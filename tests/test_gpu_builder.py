@@ -53,3 +53,21 @@ def test_rebuild_in_place(dctf):
     with pytest.raises(dctf.DctfError):
         op.rebuild(np.ones((9, 9)), (4, 4), oracle.ZERO)   # larger than the 8x8 block
     op.release()
+
+
+def test_convolution_flag_matches_scipy_convolve(dctf):
+    """DCTF_MASK_CONVOLUTION: the operator filters like scipy.ndimage.convolve
+    on each block (checked through the built M and the oracle's inverse DCT)."""
+    import scipy.ndimage as nd
+    g = np.random.default_rng(23)
+    w = g.uniform(-1, 1, (3, 5))
+    a = (1, 2)                                 # centred: scipy's default origin
+    op = dctf.build_operator(w, a, 8, dctf.REPLICATE, convolution=True)
+    m, _ = op.download()
+    blocks = g.integers(0, 256, (5, 8, 8)).astype(float)
+    y = oracle.apply_M(m, oracle.dct2_blocks(blocks))
+    p = oracle.idct2_blocks(y, 8)
+    for b in range(5):
+        ref = nd.convolve(blocks[b], w, mode="nearest")
+        assert np.abs(p[b] - ref).max() < 1e-9
+    op.release()

@@ -25,5 +25,4 @@ def test_bounded_wait_times_out_and_aborts_other_roles(dctf):
     dctf.apply(op, x, 300, y)
     torch.cuda.synchronize()
     assert torch.isfinite(y).all() and op.status() == 0
-    with pytest.raises(dctf.DctfError):
-        dctf.selftest_wait_timeout(0)
+    assert dctf.selftest_wait_timeout(0)[0] == 1             # EINVAL, nothing launched

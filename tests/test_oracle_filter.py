@@ -147,3 +147,14 @@ def test_operator_route_equals_spatial_route_fp64():
         p_dct = oracle.idct2_blocks(
             oracle.apply_M(oracle.build_M(w, a, n, boundary), oracle.dct2_blocks(blocks)), n)
         assert np.abs(p_spatial - p_dct).max() < 1e-9
+
+
+def test_convolution_is_rotated_correlation():
+    """The convolution reading of Eq. 5 equals the correlation of the oracle
+    with the rotated mask and mirrored anchor (scipy.ndimage.convolve)."""
+    g = np.random.default_rng(24)
+    w = g.uniform(-1, 1, (3, 5))
+    blocks = g.integers(0, 256, (3, 8, 8)).astype(float)
+    out = oracle.spatial_filter_blocks(blocks, w[::-1, ::-1], (3 - 1 - 1, 5 - 1 - 2), REPLICATE)
+    for b in range(3):
+        assert np.abs(out[b] - nd.convolve(blocks[b], w, mode="nearest")).max() < 1e-10
