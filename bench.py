@@ -38,13 +38,14 @@ METRIC = "filtered 8x8 blocks/s, % HBM peak (TC-split vs FP32, uint8-exact); p99
 UNIT = "blocks/s"
 WORKLOAD = "4096x4096 uint8 image, 262144 8x8 blocks, FP32 coefficients, random asymmetric 5x5 mask anchor (1,3), border replication"
 BYTES_PER_BLOCK = 512          # 256 B of FP32 coefficients in + 256 B out
+PIXEL_BYTES_PER_BLOCK = 320    # fused pixel output: 256 B of coefficients in + 64 B of uint8 out
 FLOPS_PER_BLOCK_FP32 = 2 * 64 * 64   # one 64 x 64 matrix-vector product
 ROTATE = 8
 
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "0681e5cf44b3e55699e94710c1d423c057245e32": 132014438,
+    "38f005fbda8bc8ffb3e395624837ef54f1256b5d": 132032512,
 }
 
 
@@ -62,6 +63,9 @@ def parse():
     p.add_argument("--serving-requests", type=int, default=400)
     p.add_argument("--no-workloads", action="store_true",
                    help="skip the small / grouped / 16x16 workloads")
+    p.add_argument("--workloads-only", action="store_true",
+                   help="run only the small / grouped / 16x16 workloads (rank 0) and print "
+                        "their JSON; not a bench line (for profiling them)")
     return p.parse_args()
 
 
@@ -343,12 +347,20 @@ def run_workloads(lib, torch, reps: int):
     del img
     yl = torch.empty_like(xl)
     op = lib.build_operator(job.mask, job.anchor, 16, job.boundary)
-    res = {"blocks": nb}
-    for name, prec in (("F16X3", lib.F16X3), ("FP32_SIMT", lib.FP32_SIMT)):
-        op.set_precision(prec)
+    # error of each arithmetic against the operator's own FP64 M (built on
+    # the device, equal to the paper's M to 1e-12) applied in FP64 on the
+    # host to a sample of 4096 blocks spread over the image
+    m64, _ = op.download()
+    idx = torch.linspace(0, nb - 1, 4096).long()
+    xs64 = xl[idx.to(dev)].double().cpu().numpy()
+    ys64 = xs64 @ m64.T
+    res = {"blocks": nb, "error_sample_blocks": 4096}
+    for name in ("F16X3", "BF16X6", "TF32X3", "TF32X1", "FP32_SIMT"):
+        op.set_precision(getattr(lib, name))
         t = graph_time_ms(torch, lambda s: lib.apply(op, xl, nb, yl, stream=s), max(1, reps // 4))
+        err = float(abs(yl[idx.to(dev)].double().cpu().numpy() - ys64).max())
         res[name] = {"us": 1e3 * t, "blocks_per_s": nb / (t / 1e3),
-                     "GBps": nb * 2048 / (t / 1e3) / 1e9}
+                     "GBps": nb * 2048 / (t / 1e3) / 1e9, "max_coef_err_vs_fp64": err}
     out["large_8192x8192_16x16"] = res
     op.release()
     return out
@@ -367,6 +379,10 @@ def run_dctf(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib.load()
+    if args.workloads_only:
+        if rank == 0:
+            print(json.dumps({"workloads": run_workloads(lib, torch, 40)}), flush=True)
+        return
 
     job = datagen.headline_job(args.size, args.size)
     h, w = job.image.shape
@@ -478,6 +494,31 @@ def run_dctf(args):
                 "roofline": {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
                              "frac": alu / alu_peak,
                              "peak_kind": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz max clock"}}
+    # fused coefficients -> filtered uint8 pixels (dctf_apply_pixels), the
+    # same inputs: 256 B in + 64 B out per block
+    imgs = [torch.empty((h, w), dtype=torch.uint8, device=dev) for _ in range(ROTATE)]
+
+    def pixels_graph(steps):
+        main = torch.cuda.Stream()
+        lib.apply_pixels(ops[0], xs[0], h, w, imgs[0], stream=main)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=main, capture_error_mode="thread_local"):
+            for i in range(steps):
+                lib.apply_pixels(ops[0], xs[i % ROTATE], h, w, imgs[i % ROTATE], stream=main)
+        torch.cuda.synchronize()
+        return g
+
+    px_steps = min(args.steps, 1000)
+    pixels_graph(max(args.warmup, 1)).replay()
+    px_ms, _ = run_timed(pixels_graph(px_steps))
+    px_us = 1e3 * px_ms / px_steps
+    px_gbps = PIXEL_BYTES_PER_BLOCK * nb / (px_us / 1e6) / 1e9
+    fused_pixels = {"us": px_us, "blocks_per_s": ws * nb / (px_us / 1e6), "GBps": px_gbps,
+                    "frac_of_measured_hbm": px_gbps / measured_peaks()[0],
+                    "bytes_per_block": PIXEL_BYTES_PER_BLOCK,
+                    "kernel": "apply_group_kernel<float,4,1,false,true> (pixel epilogue)"}
+    del imgs
     op = ops[0]
     op.set_precision(lib.F16X3)
     # the operator build alone (2 kernels), for the record
@@ -542,6 +583,7 @@ def run_dctf(args):
                      "apply_us_mean": 1e3 * apply_mean,
                      "timing": "events around K back-to-back applies in one CUDA graph"},
         "fp32_simt": simt,
+        "fused_pixels": fused_pixels,
         "e2e": e2e,
         "serving": serving,
         "workloads": workloads,

@@ -66,9 +66,16 @@ typedef enum { DCTF_ZERO = 0, DCTF_REPLICATE = 1 } dctf_boundary;
  *  FP32_SIMT : plain FP32 FMA on CUDA cores (comparison kernel).
  *  F16X3     : tcgen05 tensor cores, FP16 hi/lo split of x and M,
  *              hi*hi + hi*lo + lo*hi.  |x| must stay below 65504.
- *              n = 8 and n = 16 (16x16: not in place).
- *  TF32X3    : tcgen05, TF32 hi/lo split, three products (not yet built).
- *  BF16X6    : tcgen05, three BF16 pieces, six products (not yet built). */
+ *              n = 8 and n = 16.
+ *  BF16X6    : tcgen05, x and M in three BF16 pieces each, the six
+ *              products x_i m_j with i + j <= 2.  n = 16.
+ *  TF32X3    : tcgen05, TF32 hi/lo split, hi*hi + hi*lo + lo*hi.  n = 16.
+ *  TF32X1    : tcgen05, x and M rounded to TF32 once, one product; about
+ *              3 decimal digits, NOT within the 1e-3 coefficient bar (for
+ *              comparison).  n = 16.
+ * The tensor-core variants of 16x16 blocks do not run in place.
+ * dctf_operator_set_precision returns DCTF_EUNSUPPORTED for a variant that
+ * has no kernel for the operator's n. */
 typedef enum {
     DCTF_FP32_SIMT = 0,
     DCTF_F16X3 = 1,
@@ -146,10 +153,29 @@ void dctf_release_operator(dctf_operator *op);
 
 /* y_b = M x_b for b < nblocks (Eq. 11 zero padding, Eq. 20 replication).
  *  coeffs, out  device [nblocks][n2] FP32; out == coeffs (in place) allowed
- *               except for 16x16 blocks with DCTF_F16X3; no other overlap.
+ *               except for 16x16 blocks with a tensor-core precision; no
+ *               other overlap.
  * Arithmetic per dctf_operator_set_precision. */
 dctf_status dctf_apply(const dctf_operator *op, const float *coeffs,
                        int64_t nblocks, float *out, dctf_stream_t stream);
+
+/* Filtered uint8 pixels straight from the block-DCT coefficients, one pass
+ * (no counterpart kernel in the paper; its Sec. III validation converts the
+ * filtered coefficients back to uint8 pixels).  The pixel operator
+ * G = H K^T = K^T M (Eq. 3 applied after Eq. 7, K^T K = I) takes a block's
+ * coefficients to its filtered pixels; each pixel is rounded half away from
+ * zero and saturated to [0, 255].
+ *  coeffs  device [nblocks][64] FP32, nblocks = (height/8)*(width/8), raster
+ *          block order, 16-byte aligned.
+ *  image   device uint8, height rows of `pitch` bytes (pitch >= width, a
+ *          multiple of 8; 8-byte aligned); only the height x width pixels
+ *          are written.  Must not overlap coeffs.
+ * 8x8 operators only (EUNSUPPORTED otherwise); arithmetic F16X3 on tensor
+ * cores whatever the operator's precision setting; honours
+ * DCTF_APPLY_INPUTS_READY.  Asynchronous on `stream`. */
+dctf_status dctf_apply_pixels(const dctf_operator *op, const float *coeffs,
+                              int height, int width, uint8_t *image,
+                              int64_t pitch, dctf_stream_t stream);
 
 /* As dctf_apply, with FP64 input coefficients (FP32 output), FP32 SIMT
  * arithmetic; for the small FP64-coefficient workload. */

@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3",
     "DctfError", "load", "lib_path", "exported_symbols", "build_operator", "Operator",
-    "apply", "apply_f64in", "apply_host", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
+    "apply", "apply_f64in", "apply_host", "apply_pixels", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
     "version", "IO_F32", "IO_I16", "Group", "group_create", "apply_grouped", "Server",
 ]
 
@@ -45,6 +45,7 @@ _SIGS = {
     "dctf_release_operator": (None, [_vp]),
     "dctf_apply": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "dctf_apply_f64in": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "dctf_apply_pixels": (_i32, [_vp, _vp, _i32, _i32, _vp, _i64, _vp]),
     "dctf_apply_host": (_i32, [_vp, _vp, _i64, _vp]),
     "dctf_forward_dct": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
     "dctf_forward_dct_f64": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
@@ -188,6 +189,14 @@ def build_operator(mask, anchor, n: int, boundary: int, stream=None,
 def apply(op: Operator, coeffs, nblocks: int, out, stream=None) -> None:
     """out[b] = M coeffs[b] for b < nblocks (device FP32 [nblocks][n2])."""
     _check(load().dctf_apply(op.handle, _ptr(coeffs), nblocks, _ptr(out), _stream(stream)))
+
+
+def apply_pixels(op: Operator, coeffs, height: int, width: int, image,
+                 pitch: int | None = None, stream=None) -> None:
+    """Device coefficients [nblocks][64] -> filtered uint8 image (device,
+    height rows of `pitch` bytes), one fused pass (8x8 operators)."""
+    _check(load().dctf_apply_pixels(op.handle, _ptr(coeffs), height, width, _ptr(image),
+                                    pitch or width, _stream(stream)))
 
 
 def apply_f64in(op: Operator, coeffs, nblocks: int, out, stream=None) -> None:

@@ -28,6 +28,12 @@
 //  * Quantised I/O (IoT = int16_t): the converter dequantises x = Q q_in
 //    before the split, the epilogue requantises round_half_away(y / q_out)
 //    with int16 saturation, so int16 coefficients go HBM -> HBM directly.
+//  * Pixel output (kPix): the operator is G = H K^T, which takes a block's
+//    DCT coefficients straight to its filtered pixels (K^T K = I, so
+//    K^T M = H K^T, Eq. 3 applied after Eq. 7); the epilogue rounds half
+//    away from zero, saturates to [0, 255] and writes the block's 8 x 8
+//    bytes into the image (Sec. III's conversion), 64 B per block instead
+//    of 256 B of coefficients.
 //
 // Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM
 // allocator, warp 3 slot loader, warps 4-7 converter (thread = tile row),
@@ -202,7 +208,7 @@ struct TileWalk {
 // FP32 I/O: at most 152 registers a thread (58,368 of the SM's 65,536 for 384
 // threads), so the small FP64 operator-build kernels of the next image can
 // run on the same SMs while this kernel streams.
-template <typename IoT, int S, int NS, bool kGroup>
+template <typename IoT, int S, int NS, bool kGroup, bool kPix>
 __global__ void __maxnreg__(sizeof(IoT) == 4 ? 152 : 168)
 apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__ GroupItem single,
                    int nitems, int64_t total_halves, int max_take, int interleaved,
@@ -449,6 +455,35 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         acc[4 * u + 2] = fmaf(acc[4 * u + 2], out_scale, md.z * x0);
         acc[4 * u + 3] = fmaf(acc[4 * u + 3], out_scale, md.w * x0);
       }
+      if constexpr (kPix) {
+        // block b of the item covers image rows 8 (b / bw) + 0..7 and columns
+        // 8 (b % bw) + 0..7; its pixel (i, j) is output i * 8 + j.  The lanes
+        // of a warp hold consecutive blocks, so each row's 8-byte stores of a
+        // warp are contiguous.
+        const int64_t b = (int64_t)t.row0 + row;
+        if (row < t.rows && b < gi.nblocks) {
+          const int64_t by = b / gi.bw, bx = b - by * gi.bw;
+          uint8_t *dst = gi.img + by * 8 * gi.pitch + bx * 8;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            uint32_t w[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              uint32_t v = 0;
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float p = fminf(fmaxf(roundf(acc[8 * i + 4 * h + e]), 0.f), 255.f);
+                v |= (uint32_t)p << (8 * e);
+              }
+              w[h] = v;
+            }
+            *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
+          }
+        }
+        if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's G[:,0]
+        ++it;
+        continue;
+      }
       const bool store = wr * 32 < t.rows;
       if (lane == 0) bulk_wait_read<1>();             // slab o free (store of tile it-2 read it)
       __syncwarp();
@@ -542,11 +577,11 @@ cudaError_t make_map(CUtensorMap *m, const void *ptr, int64_t nblocks, bool i16,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <typename IoT, int S, int NS, bool kGroup>
+template <typename IoT, int S, int NS, bool kGroup, bool kPix = false>
 cudaError_t launch_cfg(const GroupItem *d_items, const GroupItem &single, int nitems,
                        int64_t total_halves, int grid, int max_take, int interleaved,
                        uint32_t *err, cudaStream_t s, bool pdl) {
-  auto kern = apply_group_kernel<IoT, S, NS, kGroup>;
+  auto kern = apply_group_kernel<IoT, S, NS, kGroup, kPix>;
   constexpr int smem = Layout<IoT, S, NS>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -585,6 +620,16 @@ cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *
   gi->out_scale = ldexpf(1.0f, -op->f16_scale_exp);
   gi->nblocks = nblocks;
   return cudaSuccess;
+}
+
+cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, int grid,
+                                uint32_t *err, cudaStream_t s, bool pdl) {
+  if (total_halves <= 0) return cudaSuccess;
+  int64_t g = grid > 0 ? grid : 0;
+  if (g > total_halves) g = total_halves;
+  if (g < 1) g = 1;
+  return launch_cfg<float, 4, 1, false, true>(nullptr, single, 1, total_halves, (int)g, 2, 1, err,
+                                              s, pdl);
 }
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,

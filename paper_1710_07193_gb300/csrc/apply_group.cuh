@@ -25,6 +25,9 @@ struct GroupItem {              // CUtensorMap members keep it 128-byte aligned
   int pad0;
   int64_t nblocks;
   int64_t half_begin;       // first 64-block half tile of the item in the group
+  uint8_t *img;             // pixel output (apply_pixels): uint8 image,
+  int64_t pitch;            //   its row pitch in bytes,
+  int64_t bw;               //   and its width in blocks
 };
 
 cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *in, void *out,
@@ -35,6 +38,12 @@ cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *
 // passed by value.  grid <= 0 means one CTA per SM.  max_take: 2 for 128-row
 // tiles, 1 for 64-row tiles.  pdl: launch with programmatic stream
 // serialisation (the inputs must not be written by the preceding kernel).
+// Fused pixel output, one item: the item's pieces and mdc are those of the
+// pixel operator G = H K^T (and G[:, 0]); the epilogue writes uint8 pixels
+// into item.img instead of coefficients.
+cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, int grid,
+                                uint32_t *err, cudaStream_t s, bool pdl);
+
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,
                                uint32_t *err, cudaStream_t s, bool pdl = false);

@@ -1,24 +1,38 @@
-// Tensor-core apply for 16x16 blocks (N^2 = 256): y_b = M x_b, F16X3 split.
+// Tensor-core apply for 16x16 blocks (N^2 = 256): y_b = M x_b with a split
+// precision, one kernel template per split.
 //
-// Same arithmetic as the 8x8 kernel (apply_group.cu): x and M 2^s split into
-// FP16 hi/lo, y = (x_hi M_lo + x_lo M_hi + x_hi M_hi) 2^-s + M[:,0] x[0] with
-// FP32 accumulation in TMEM and the input DC coefficient in FP32.  What
-// changes at 16x16 is size: M is 256 x 256, its two FP16 pieces 256 KB,
-// more than one SM's shared memory, and a 128-block tile is 128 KB in and
-// 128 KB out.  So:
+// Every split writes x (the input coefficients, FP32) and M as sums of
+// low-precision pieces, x = sum_i x_i and M = sum_j m_j, and accumulates
+// the products x_i m_j^T that carry the result to FP32 accuracy, in FP32 in
+// TMEM; the input DC coefficient is left out of the products and added as
+// M[:,0] x[0] in FP32 in the epilogue (it is ~16x the block mean, by far the
+// largest input).  The splits:
 //
-//  * Output split.  Each 128-block tile is processed by a pair of CTAs; CTA
-//    (pair, half) computes output coefficients [128 half, 128 half + 128).
-//    Its 128 rows of M_hi and M_lo (128 KB) stay resident in shared memory
-//    for the whole launch.  Both CTAs of a pair read the same input tile
-//    (the second read is an L2 hit); each writes its own half of the output.
+//   F16X3  : x, M 2^s in FP16 hi + lo; hi.lo, lo.hi, hi.hi          (kind::f16)
+//   BF16X6 : x, M in three BF16 pieces; the six products with
+//            i + j <= 2                                              (kind::f16, bf16)
+//   TF32X3 : x, M in TF32 hi + lo; hi.lo, lo.hi, hi.hi              (kind::tf32)
+//   TF32X1 : x, M rounded to TF32 once; one product (not exact)     (kind::tf32)
+//
+// Tensor-core FP32 accumulation truncates, so the order matters: per K half
+// of 128 inputs, each with its own accumulator, the correction products go
+// in first (while the accumulator is small), the main product x_0 m_0 last;
+// the epilogue adds the two halves with round-to-nearest.
+//
+// What 16x16 changes against the 8x8 kernel (apply_group.cu) is size: M is
+// 256 x 256, its pieces 256-512 KB, more than one SM's shared memory, and a
+// 128-block tile is 128 KB in and 128 KB out.  So:
+//
+//  * Output split.  A 128-block tile is processed by kParts = 256 / kOut
+//    CTAs; CTA (group, part) computes output coefficients
+//    [kOut part, kOut part + kOut).  Its kOut rows of every M piece stay
+//    resident in shared memory for the whole launch (96-128 KB).  The CTAs
+//    of a group read the same input tile (the later reads are L2 hits); each
+//    writes its own slice of the output.
 //  * K chunks.  The tile's input is streamed in eight 32-coefficient chunks
 //    (16 KB, one SWIZZLE_128B box) through a TMA ring; the converter turns
-//    each chunk into FP16 hi/lo A operands in an 8-deep TMEM ring (one whole
-//    tile), and the MMA warp accumulates 128 x 128 x 16 MMAs into two TMEM
-//    accumulators, one per K half, correction products before the main
-//    product (tensor-core FP32 accumulation truncates; this order and the
-//    split keep the error near the 8x8 kernel's).
+//    each chunk into the A pieces in a TMEM ring, and the MMA warp issues
+//    128 x kOut x K MMAs into the two accumulators of the tile.
 //  * Output chunks.  The epilogue reads D 32 columns at a time and TMA-stores
 //    32 x 32 boxes, double-buffered per warp.
 //
@@ -34,97 +48,201 @@ namespace {
 
 using namespace ptx;
 
+// ------------------------------------------------------------ the splits
+// kPieces     : pieces of x and of M
+// kImgPieces  : pieces stacked per chunk in the operator's piece image
+// kTf32       : TF32 pieces (kind::tf32), else 16-bit pieces (kind::f16)
+// kOut, kDBufs: outputs per CTA, accumulator sets (tiles) in TMEM
+// kCorr       : correction products; corr_x(j), corr_m(j) their pieces
+struct SplitF16x3 {
+  static constexpr int kPieces = 2, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 2;
+  static constexpr bool kTf32 = false, kBf16 = false;
+  __device__ static constexpr int corr_x(int j) { return j; }
+  __device__ static constexpr int corr_m(int j) { return 1 - j; }
+};
+struct SplitBf16x6 {
+  static constexpr int kPieces = 3, kImgPieces = 3, kOut = 64, kDBufs = 2, kCorr = 5;
+  static constexpr bool kTf32 = false, kBf16 = true;
+  // (0,2) (1,1) (2,0) (0,1) (1,0): second-order terms before first-order
+  __device__ static constexpr int corr_x(int j) { return j < 3 ? j : j - 3; }
+  __device__ static constexpr int corr_m(int j) { return j < 3 ? 2 - j : 4 - j; }
+};
+struct SplitTf32x3 {
+  static constexpr int kPieces = 2, kImgPieces = 2, kOut = 64, kDBufs = 2, kCorr = 2;
+  static constexpr bool kTf32 = true, kBf16 = false;
+  __device__ static constexpr int corr_x(int j) { return j; }
+  __device__ static constexpr int corr_m(int j) { return 1 - j; }
+};
+struct SplitTf32x1 {
+  static constexpr int kPieces = 1, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 0;
+  static constexpr bool kTf32 = true, kBf16 = false;
+  __device__ static constexpr int corr_x(int) { return 0; }
+  __device__ static constexpr int corr_m(int) { return 0; }
+};
+
 constexpr int kThreads = 384;
 constexpr int kTile = 128;
 constexpr int kN2 = 256;                 // coefficients per block
-constexpr int kOut = 128;                // outputs per CTA (half of kN2)
 constexpr int kChunkK = 32;              // K per input chunk (one 128-byte box row)
 constexpr int kChunks = kN2 / kChunkK;   // 8
+constexpr int kGroups = 2;               // K halves, each with its own accumulator
 constexpr int kStages = 3;               // input chunk stages
-constexpr int kABufs = 8;                // TMEM A ring (one chunk each: hi 16 | lo 16 columns)
-constexpr int kGroups = 2;               // K halves, each with its own 128-column accumulator
 constexpr int kDcRing = 8;
 constexpr uint32_t kTmemCols = 512;
-
+constexpr uint32_t kRingCols = 256;      // A ring: columns 0..255; accumulators 256..511
 constexpr int kChunkBytes = kTile * kChunkK * 4;    // 16 KB: one box (32 floats x 128 rows)
-constexpr int kBChunks = kN2 / 64;                  // 64-wide K blocks of the B layout
-constexpr int kBPieceChunk = kOut * 128;            // 16 KB: 128 rows x 64 fp16
-constexpr int kBBytes = 2 * kBChunks * kBPieceChunk; // 128 KB: [piece][kb][128 rows][128 B]
 constexpr int kOutSlab = 32 * 128;                  // one warp's 32 x 32 floats box
-constexpr int kOffB = 0;
-constexpr int kOffIn = kOffB + kBBytes;
-constexpr int kOffOut = kOffIn + kStages * kChunkBytes;
-constexpr int kOffMdc = kOffOut + 2 * 4 * kOutSlab;
-constexpr int kOffDc = kOffMdc + kOut * 4;
-constexpr int kOffBar = kOffDc + kDcRing * kTile * 4;
-constexpr int kNumBars = 2 * kStages + 2 * kABufs + 2 + kDcRing;
-constexpr int kOffMisc = kOffBar + kNumBars * 8;
-constexpr int kSmem = kOffMisc + 16 + 1024;
-static_assert(kSmem <= 232448, "shared memory");
+
+template <class S>
+struct Layout {
+  static constexpr int kElem = S::kTf32 ? 4 : 2;            // bytes per piece element
+  static constexpr int kRowElems = 128 / kElem;             // K per 128-byte B row
+  static constexpr int kBlocksK = kN2 / kRowElems;          // 128-byte K blocks of B
+  static constexpr int kPieceCols = kChunkK * kElem / 4;    // TMEM columns per A piece per chunk
+  static constexpr int kABufCols = S::kPieces * kPieceCols;
+  static constexpr int kABufs = kRingCols / kABufCols;
+  static constexpr int kKStep = S::kTf32 ? 8 : 16;          // K per MMA
+  static constexpr int kParts = kN2 / S::kOut;
+  static constexpr int kBBlock = S::kOut * 128;             // one (piece, K block) of B
+  static constexpr int kBBytes = S::kPieces * kBlocksK * kBBlock;
+  static constexpr int kOffB = 0;
+  static constexpr int kOffIn = kOffB + kBBytes;
+  static constexpr int kOffOut = kOffIn + kStages * kChunkBytes;
+  static constexpr int kOffMdc = kOffOut + 2 * 4 * kOutSlab;
+  static constexpr int kOffDc = kOffMdc + S::kOut * 4;
+  static constexpr int kOffBar = kOffDc + kDcRing * kTile * 4;
+  static constexpr int kNumBars = 2 * kStages + 2 * kABufs + 2 * S::kDBufs + kDcRing;
+  static constexpr int kOffMisc = kOffBar + kNumBars * 8;
+  static constexpr int kSmem = kOffMisc + 16 + 1024;
+  static_assert(kSmem <= 232448, "shared memory");
+  static_assert(kABufs >= kChunks / kGroups, "a K half's chunks must fit the A ring");
+  static_assert(S::kDBufs * kGroups * S::kOut == (int)(kTmemCols - kRingCols), "TMEM split");
+  static_assert(kDcRing >= S::kDBufs + 2, "DC ring depth");
+  static_assert(!(S::kTf32 && S::kBf16), "one piece type");
+};
 
 enum : uint32_t { kRoleProducer = 1, kRoleMma = 2, kRoleConv = 3, kRoleEpi = 4, kRoleDrain = 5 };
 
+// Split one chunk row (32 FP32 inputs) into the A pieces and store them to
+// this lane's TMEM row at column t_a (piece p at t_a + p kPieceCols).
+template <class S>
+__device__ __forceinline__ void convert_store(const float (&v)[32], uint32_t t_a) {
+  if constexpr (S::kTf32) {
+    uint32_t hi[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) hi[c] = tf32_rna(v[c]);
+    tmem_st32(t_a, hi);
+    if constexpr (S::kPieces == 2) {
+      uint32_t lo[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) lo[c] = tf32_rna(v[c] - __uint_as_float(hi[c]));
+      tmem_st32(t_a + 32, lo);
+    }
+  } else if constexpr (S::kBf16) {
+    // x = x0 + x1 + x2 exactly (FP32 has 24 bits, each BF16 piece takes 8)
+    uint32_t p0[16], p1[16], p2[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float a0 = v[2 * c], a1 = v[2 * c + 1];
+      const __nv_bfloat162 b0 = __floats2bfloat162_rn(a0, a1);
+      const float2 f0 = __bfloat1622float2(b0);
+      const float r0 = a0 - f0.x, r1 = a1 - f0.y;
+      const __nv_bfloat162 b1 = __floats2bfloat162_rn(r0, r1);
+      const float2 f1 = __bfloat1622float2(b1);
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(r0 - f1.x, r1 - f1.y);
+      p0[c] = *reinterpret_cast<const uint32_t *>(&b0);
+      p1[c] = *reinterpret_cast<const uint32_t *>(&b1);
+      p2[c] = *reinterpret_cast<const uint32_t *>(&b2);
+    }
+    tmem_st16(t_a, p0);
+    tmem_st16(t_a + 16, p1);
+    tmem_st16(t_a + 32, p2);
+  } else {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float a0 = v[2 * c], a1 = v[2 * c + 1];
+      const __half2 h2 = __floats2half2_rn(a0, a1);
+      const float2 hf = __half22float2(h2);
+      const __half2 l2 = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
+      hi[c] = *reinterpret_cast<const uint32_t *>(&h2);
+      lo[c] = *reinterpret_cast<const uint32_t *>(&l2);
+    }
+    tmem_st16(t_a, hi);
+    tmem_st16(t_a + 16, lo);
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
+  if constexpr (S::kTf32)
+    mma_tf32_ts(d, a, b, idesc_tf32(128, S::kOut), acc);
+  else
+    mma_f16_ts(d, a, b, idesc_f16(128, S::kOut, S::kBf16), acc);
+}
+
+template <class S>
 __global__ void __launch_bounds__(kThreads, 1)
-apply_n16_f16x3_kernel(const __grid_constant__ CUtensorMap tm_in,
-                       const __grid_constant__ CUtensorMap tm_out, const uint4 *__restrict__ pieces,
-                       const float *__restrict__ Mdc, float out_scale, int ntiles,
-                       uint32_t *__restrict__ err) {
+apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_out,
+                 const uint4 *__restrict__ pieces, const float *__restrict__ Mdc, float out_scale,
+                 int ntiles, uint32_t *__restrict__ err) {
+  using L = Layout<S>;
+  constexpr int kOut = S::kOut, kABufs = L::kABufs, kDBufs = S::kDBufs;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t *s_b = base + kOffB;
-  uint8_t *s_in = base + kOffIn;
-  uint8_t *s_out = base + kOffOut;
-  float *s_mdc = reinterpret_cast<float *>(base + kOffMdc);
-  float *s_dc = reinterpret_cast<float *>(base + kOffDc);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(base + kOffBar);
+  uint8_t *s_b = base + L::kOffB;
+  uint8_t *s_in = base + L::kOffIn;
+  uint8_t *s_out = base + L::kOffOut;
+  float *s_mdc = reinterpret_cast<float *>(base + L::kOffMdc);
+  float *s_dc = reinterpret_cast<float *>(base + L::kOffDc);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + L::kOffBar);
   uint64_t *full_in = bars;                     // [kStages]
   uint64_t *empty_in = full_in + kStages;       // [kStages]
   uint64_t *a_full = empty_in + kStages;        // [kABufs]
   uint64_t *a_done = a_full + kABufs;           // [kABufs] MMA finished reading the chunk
-  uint64_t *d_full = a_done + kABufs;           // [1]
-  uint64_t *d_empty = d_full + 1;               // [1]
-  uint64_t *dc_full = d_empty + 1;              // [kDcRing]
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(base + kOffMisc);
-  volatile int *s_abort = reinterpret_cast<volatile int *>(base + kOffMisc + 4);
+  uint64_t *d_full = a_done + kABufs;           // [kDBufs]
+  uint64_t *d_empty = d_full + kDBufs;          // [kDBufs]
+  uint64_t *dc_full = d_empty + kDBufs;         // [kDcRing]
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(base + L::kOffMisc);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(base + L::kOffMisc + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int half = blockIdx.x & 1;
-  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-  const int my_tiles = pair < ntiles ? (ntiles - pair + npairs - 1) / npairs : 0;
+  const int part = blockIdx.x % L::kParts;
+  const int grp = blockIdx.x / L::kParts, ngroups = gridDim.x / L::kParts;
+  const int my_tiles = grp < ntiles ? (ntiles - grp + ngroups - 1) / ngroups : 0;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(&full_in[s], 1); mbar_init(&empty_in[s], 128); }
     for (int a = 0; a < kABufs; ++a) { mbar_init(&a_full[a], 128); mbar_init(&a_done[a], 1); }
-    mbar_init(d_full, 1);
-    mbar_init(d_empty, 128);
+    for (int d = 0; d < kDBufs; ++d) { mbar_init(&d_full[d], 1); mbar_init(&d_empty[d], 128); }
     for (int r = 0; r < kDcRing; ++r) mbar_init(&dc_full[r], 128);
     *s_abort = 0;
     mbar_fence_init();
     tma_prefetch_map(&tm_in);
   }
-  // resident B: for each piece (hi, lo) and K chunk, this half's 128 rows
-  // (a contiguous 16 KB block of the operator's piece image)
-  for (int i = tid; i < kBBytes / 16; i += kThreads) {
-    const int blk = i / (kBPieceChunk / 16), off = i % (kBPieceChunk / 16);
-    const int piece = blk / kBChunks, kc = blk % kBChunks;
-    // source image: [kc][512 rows: hi 0..255, lo 256..511][128 B]
-    const size_t src_row0 = (size_t)kc * 512 + piece * 256 + half * kOut;
+  // resident B: for each piece and 128-byte K block, this part's kOut rows
+  // (a contiguous block of the operator's piece image, whose K block kb
+  // holds kImgPieces * 256 rows: piece p's output t at row p * 256 + t)
+  for (int i = tid; i < L::kBBytes / 16; i += kThreads) {
+    const int blk = i / (L::kBBlock / 16), off = i % (L::kBBlock / 16);
+    const int piece = blk / L::kBlocksK, kb = blk % L::kBlocksK;
+    const size_t src_row0 = (size_t)kb * S::kImgPieces * kN2 + piece * kN2 + part * kOut;
     reinterpret_cast<uint4 *>(s_b)[i] = __ldg(pieces + src_row0 * 8 + off);
   }
-  if (tid < kOut) s_mdc[tid] = __ldg(Mdc + half * kOut + tid);
+  if (tid < kOut) s_mdc[tid] = __ldg(Mdc + part * kOut + tid);
   fence_async_smem();
   if (warp == 2) { tmem_alloc(s_tmem, kTmemCols); tmem_relinquish(); }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *s_tmem;   // A ring: columns 0..255, D0: 256..383, D1: 384..511
+  const uint32_t tmem = *s_tmem;
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
     int q = 0, issued = 0;
     for (int it = 0; it < my_tiles; ++it) {
-      const int tile = pair + it * npairs;
+      const int tile = grp + it * ngroups;
       for (int kc = 0; kc < kChunks; ++kc, ++q) {
         const int s = q % kStages;
         if (!wait_bounded(&empty_in[s], ((q / kStages) & 1) ^ 1, s_abort, err,
@@ -140,52 +258,52 @@ apply_n16_f16x3_kernel(const __grid_constant__ CUtensorMap tm_in,
       wait_drain(&full_in[k % kStages], (k / kStages) & 1, err, kRoleDrain);
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
-    // Tile t: for each K half g, D_g = sum over its 4 chunks of the two
-    // correction products, then of the main product.  Tensor-core FP32
-    // accumulation truncates, so small terms go in while D_g is still small,
-    // and each accumulator sees half the K steps; the epilogue adds D_0 + D_1
-    // with round-to-nearest.  The chunk's A buffer is released after its main
-    // product.
-    constexpr uint32_t kIdesc = idesc_f16(128, kOut, false);
+    // Tile t, K half g: D_g = sum over its 4 chunks of the correction
+    // products, then of the main product; a chunk's A buffer is released
+    // after its main product.
     int q = 0, last_q = -1;
     for (int it = 0; it < my_tiles; ++it) {
-      if (!wait_bounded(d_empty, (it & 1) ^ 1, s_abort, err, kRoleMma | (it << 8)))
+      const int db = it % kDBufs;
+      if (!wait_bounded(&d_empty[db], ((it / kDBufs) & 1) ^ 1, s_abort, err, kRoleMma | (it << 8)))
         goto mma_done_label;
       for (int g = 0; g < kGroups; ++g) {
-        const uint32_t t_d = tmem + 256 + g * kOut;
+        const uint32_t t_d = tmem + kRingCols + (db * kGroups + g) * kOut;
         const int q0 = q + g * (kChunks / kGroups);
         for (int c = 0; c < kChunks / kGroups; ++c) {
           const int qc = q0 + c, a = qc % kABufs, kc = g * (kChunks / kGroups) + c;
           if (!wait_bounded(&a_full[a], (qc / kABufs) & 1, s_abort, err, kRoleMma | (qc << 8)))
             goto mma_done_label;
           tc_fence_after();
-          const uint32_t t_a = tmem + a * 32;
-          // chunk kc covers K [32 kc, 32 kc + 32): 64-wide block kc / 2 of the
-          // B layout, starting 64 bytes into its rows for odd kc
-          const int kb = kc >> 1, kofs = (kc & 1) * 4;      // in 16-byte descriptor units
-          const uint64_t b_hi = desc_sw128(smem_u32(s_b + (0 * kBChunks + kb) * kBPieceChunk)) + kofs;
-          const uint64_t b_lo = desc_sw128(smem_u32(s_b + (1 * kBChunks + kb) * kBPieceChunk)) + kofs;
+          const uint32_t t_a = tmem + a * L::kABufCols;
+          // chunk kc covers K [32 kc, 32 kc + 32): K block kc * 32 / kRowElems
+          // of B, starting (kc * 32 % kRowElems) elements into its rows
+          const int kb = kc * kChunkK / L::kRowElems;
+          const int kofs = (kc * kChunkK % L::kRowElems) * L::kElem / 16;   // 16-byte units
 #pragma unroll
-          for (int kk = 0; kk < kChunkK / 16; ++kk)
-            mma_f16_ts(t_d, t_a + 8 * kk, b_lo + 2 * kk, kIdesc, (c > 0 || kk > 0) ? 1u : 0u);
+          for (int j = 0; j < S::kCorr; ++j) {
+            const uint64_t b = desc_sw128(smem_u32(
+                                   s_b + (S::corr_m(j) * L::kBlocksK + kb) * L::kBBlock)) + kofs;
 #pragma unroll
-          for (int kk = 0; kk < kChunkK / 16; ++kk)
-            mma_f16_ts(t_d, t_a + 16 + 8 * kk, b_hi + 2 * kk, kIdesc, 1);
+            for (int kk = 0; kk < kChunkK / L::kKStep; ++kk)
+              mma_ts<S>(t_d, t_a + S::corr_x(j) * L::kPieceCols + 8 * kk, b + 2 * kk,
+                        (c > 0 || j > 0 || kk > 0) ? 1u : 0u);
+          }
         }
         for (int c = 0; c < kChunks / kGroups; ++c) {
           const int qc = q0 + c, a = qc % kABufs, kc = g * (kChunks / kGroups) + c;
-          const uint32_t t_a = tmem + a * 32;
-          const int kb = kc >> 1, kofs = (kc & 1) * 4;
-          const uint64_t b_hi = desc_sw128(smem_u32(s_b + (0 * kBChunks + kb) * kBPieceChunk)) + kofs;
+          const uint32_t t_a = tmem + a * L::kABufCols;
+          const int kb = kc * kChunkK / L::kRowElems;
+          const int kofs = (kc * kChunkK % L::kRowElems) * L::kElem / 16;
+          const uint64_t b = desc_sw128(smem_u32(s_b + kb * L::kBBlock)) + kofs;
 #pragma unroll
-          for (int kk = 0; kk < kChunkK / 16; ++kk)
-            mma_f16_ts(t_d, t_a + 8 * kk, b_hi + 2 * kk, kIdesc, 1);
+          for (int kk = 0; kk < kChunkK / L::kKStep; ++kk)
+            mma_ts<S>(t_d, t_a + 8 * kk, b + 2 * kk, (S::kCorr > 0 || c > 0 || kk > 0) ? 1u : 0u);
           tc_commit(&a_done[a]);
           last_q = qc;
         }
       }
       q += kChunks;
-      tc_commit(d_full);
+      tc_commit(&d_full[db]);
     }
   mma_done_label:
     if (last_q >= 0) wait_drain(&a_done[last_q % kABufs], (last_q / kABufs) & 1, err, kRoleDrain);
@@ -208,8 +326,12 @@ apply_n16_f16x3_kernel(const __grid_constant__ CUtensorMap tm_in,
         }
         mbar_arrive(&empty_in[s]);
         if (kc == 0) {
+          // ring slot it % kDcRing is free: to get here the converter waited
+          // for the MMAs of a chunk of tile it - 2 or later, which began
+          // after the epilogue had read tile it - 2 - kDBufs, so at most
+          // kDBufs + 1 earlier tiles still hold slots (kDcRing >= kDBufs + 2)
           const int r = it % kDcRing;
-          s_dc[r * kTile + row] = v[0];     // ring slot free: see the epilogue's d_empty chain
+          s_dc[r * kTile + row] = v[0];
           v[0] = 0.f;
           mbar_arrive(&dc_full[r]);
         }
@@ -218,21 +340,7 @@ apply_n16_f16x3_kernel(const __grid_constant__ CUtensorMap tm_in,
                                kRoleConv | (q << 8)))
           goto conv_done;
         tc_fence_after();
-        const uint32_t t_a = tmem + lane_base + a * 32;
-        {
-          uint32_t hi[16], lo[16];
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const float a0 = v[2 * c], a1 = v[2 * c + 1];
-            const __half2 h2 = __floats2half2_rn(a0, a1);
-            const float2 hf = __half22float2(h2);
-            const __half2 l2 = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
-            hi[c] = *reinterpret_cast<const uint32_t *>(&h2);
-            lo[c] = *reinterpret_cast<const uint32_t *>(&l2);
-          }
-          tmem_st16(t_a, hi);
-          tmem_st16(t_a + 16, lo);
-        }
+        convert_store<S>(v, tmem + lane_base + a * L::kABufCols);
         tmem_st_wait();
         tc_fence_before();
         mbar_arrive(&a_full[a]);
@@ -245,20 +353,21 @@ apply_n16_f16x3_kernel(const __grid_constant__ CUtensorMap tm_in,
     const uint32_t lane_base = (uint32_t)(wr * 32) << 16;
     int o = 0;
     for (int it = 0; it < my_tiles; ++it) {
-      const int tile = pair + it * npairs;
-      const int r = it % kDcRing;
-      if (!warp_wait_bounded(d_full, it & 1, s_abort, err, kRoleEpi | (it << 8))) break;
+      const int tile = grp + it * ngroups;
+      const int r = it % kDcRing, db = it % kDBufs;
+      if (!warp_wait_bounded(&d_full[db], (it / kDBufs) & 1, s_abort, err, kRoleEpi | (it << 8)))
+        break;
       tc_fence_after();
       if (!warp_wait_bounded(&dc_full[r], (it / kDcRing) & 1, s_abort, err, kRoleEpi | (it << 8)))
         break;
       const float x0 = s_dc[r * kTile + row];
-      const uint32_t t_d = tmem + lane_base + 256;
+      const uint32_t t_d = tmem + lane_base + kRingCols + db * kGroups * kOut;
       for (int j = 0; j < kOut / 32; ++j, ++o) {
         uint32_t d0[32], d1[32];
         tmem_ld32x2(t_d + 32 * j, t_d + kOut + 32 * j, d0, d1);
         if (j == kOut / 32 - 1) {
           tc_fence_before();
-          mbar_arrive(d_empty);                // every column of D_0 and D_1 has been read
+          mbar_arrive(&d_empty[db]);           // every column of this tile's D has been read
         }
         if (lane == 0) bulk_wait_read<1>();   // staging box o & 1 free
         __syncwarp();
@@ -279,7 +388,7 @@ apply_n16_f16x3_kernel(const __grid_constant__ CUtensorMap tm_in,
         fence_async_smem();
         __syncwarp();
         if (lane == 0) {
-          tma_store_2d(&tm_out, slab, half * kOut + 32 * j, tile * kTile + wr * 32);
+          tma_store_2d(&tm_out, slab, part * kOut + 32 * j, tile * kTile + wr * 32);
           bulk_commit();
         }
       }
@@ -328,25 +437,44 @@ cudaError_t make_map(CUtensorMap *m, const void *ptr, int64_t nblocks, int box_r
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+template <class S>
+cudaError_t launch(const dctf_operator *op, const void *pieces, float out_scale,
+                   const CUtensorMap &tin, const CUtensorMap &tout, int ntiles, cudaStream_t s) {
+  using L = Layout<S>;
+  cudaError_t e = cudaFuncSetAttribute(apply_n16_kernel<S>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem);
+  if (e != cudaSuccess) return e;
+  int groups = sm_count(op->device) / L::kParts;
+  if (groups > ntiles) groups = ntiles;
+  if (groups < 1) groups = 1;
+  apply_n16_kernel<S><<<L::kParts * groups, kThreads, L::kSmem, s>>>(
+      tin, tout, reinterpret_cast<const uint4 *>(pieces), op->d_Mdc, out_scale, ntiles, op->d_err);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
                              cudaStream_t s) {
+  if (op->d_f16 == nullptr || op->d_bf16 == nullptr || op->d_tf32 == nullptr)
+    return cudaErrorInvalidValue;
   CUtensorMap tin, tout;
   cudaError_t e = make_map(&tin, x, nblocks, kTile);
   if (e == cudaSuccess) e = make_map(&tout, y, nblocks, 32);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(apply_n16_f16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kSmem);
-  if (e != cudaSuccess) return e;
   const int ntiles = (int)((nblocks + kTile - 1) / kTile);
-  int pairs = sm_count(op->device) / 2;
-  if (pairs > ntiles) pairs = ntiles;
-  if (pairs < 1) pairs = 1;
-  apply_n16_f16x3_kernel<<<2 * pairs, kThreads, kSmem, s>>>(
-      tin, tout, reinterpret_cast<const uint4 *>(op->d_f16), op->d_Mdc,
-      ldexpf(1.0f, -op->f16_scale_exp), ntiles, op->d_err);
-  return cudaGetLastError();
+  switch (op->precision) {
+    case DCTF_F16X3:
+      return launch<SplitF16x3>(op, op->d_f16, ldexpf(1.0f, -op->f16_scale_exp), tin, tout, ntiles, s);
+    case DCTF_BF16X6:
+      return launch<SplitBf16x6>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s);
+    case DCTF_TF32X3:
+      return launch<SplitTf32x3>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s);
+    case DCTF_TF32X1:
+      return launch<SplitTf32x1>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace dctf

@@ -11,12 +11,14 @@
 // Two launches, both one CTA per row/column of an N^2 x N^2 matrix:
 //   build_hg: row p of H (a1) and row p of G = H K^T (first half of a2);
 //   build_m : column q of M = K G (second half of a2), its FP32 copy and the
-//             FP16 hi/lo pieces (a3), written in the tensor-core B layout.
+//             low-precision pieces (a3) in the tensor-core B layout: FP16
+//             hi/lo, and for 16x16 blocks also three BF16 pieces and TF32
+//             hi/lo.
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
-#include "dctf_internal.cuh"
+#include "sm100_ptx.cuh"
 
 namespace dctf {
 namespace {
@@ -100,7 +102,9 @@ __global__ void build_hg_kernel(const MaskParams mp, const double *__restrict__ 
 __global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restrict__ C,
                                const double *__restrict__ G, double *__restrict__ M64,
                                float *__restrict__ M32, float *__restrict__ Mdc,
-                               __half *__restrict__ f16) {
+                               __half *__restrict__ f16, __nv_bfloat16 *__restrict__ bf16,
+                               uint32_t *__restrict__ tf32, __half *__restrict__ f16_pix,
+                               float *__restrict__ Gdc) {
   __shared__ double cs[kMaxN][kMaxN + 1];
   __shared__ double gcol[kMaxN2];
   __shared__ double tmp[kMaxN2];
@@ -111,6 +115,18 @@ __global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restric
   // M[:][q] = K G[:][q] = vec(C mat(G[:][q]) C^T)
   double m = dct2_vec(gcol, tmp, cs, n, t);
   if (t >= n2) return;
+  if (f16_pix != nullptr) {
+    // the pixel operator G = H K^T (coefficients -> filtered pixels), split
+    // like M: G 2^s = hi + lo in FP16 (|G| obeys the same bound as |M|)
+    const double gs = ldexp(gcol[t], f16_scale_exp);
+    const __half hi = __double2half(gs);
+    const __half lo = __double2half(gs - (double)__half2float(hi));
+    const int chunk = q >> 6, byte = (q & 63) * 2;
+    char *base = reinterpret_cast<char *>(f16_pix);
+    *reinterpret_cast<__half *>(base + sw128_offset(t, byte, 2 * n2, chunk)) = hi;
+    *reinterpret_cast<__half *>(base + sw128_offset(n2 + t, byte, 2 * n2, chunk)) = lo;
+    if (q == 0) Gdc[t] = (float)gcol[t];
+  }
   M64[(size_t)t * n2 + q] = m;
   M32[(size_t)t * n2 + q] = (float)m;
   if (q == 0) Mdc[t] = (float)m;
@@ -124,6 +140,31 @@ __global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restric
     char *base = reinterpret_cast<char *>(f16);
     *reinterpret_cast<__half *>(base + sw128_offset(t, byte, 2 * n2, chunk)) = hi;
     *reinterpret_cast<__half *>(base + sw128_offset(n2 + t, byte, 2 * n2, chunk)) = lo;
+  }
+  if (bf16 != nullptr) {
+    // M = m0 + m1 + m2 + O(2^-24 |M|), each piece the BF16 rounding of the
+    // remainder (FP64 arithmetic, so every remainder is exact); rows
+    // p n2 + t, 64 inputs per 128-byte row.  BF16 has FP32's exponent range,
+    // so no scaling.
+    const __nv_bfloat16 b0 = __double2bfloat16(m);
+    const double r1 = m - (double)__bfloat162float(b0);
+    const __nv_bfloat16 b1 = __double2bfloat16(r1);
+    const __nv_bfloat16 b2 = __double2bfloat16(r1 - (double)__bfloat162float(b1));
+    const int chunk = q >> 6, byte = (q & 63) * 2;
+    char *base = reinterpret_cast<char *>(bf16);
+    *reinterpret_cast<__nv_bfloat16 *>(base + sw128_offset(t, byte, 3 * n2, chunk)) = b0;
+    *reinterpret_cast<__nv_bfloat16 *>(base + sw128_offset(n2 + t, byte, 3 * n2, chunk)) = b1;
+    *reinterpret_cast<__nv_bfloat16 *>(base + sw128_offset(2 * n2 + t, byte, 3 * n2, chunk)) = b2;
+  }
+  if (tf32 != nullptr) {
+    // M = hi + lo + O(2^-22 |M|) in TF32 (FP32 bit patterns, low 13 bits
+    // clear); rows p n2 + t, 32 inputs per 128-byte row.
+    const uint32_t hi = ptx::tf32_rna((float)m);
+    const uint32_t lo = ptx::tf32_rna((float)(m - (double)__uint_as_float(hi)));
+    const int chunk = q >> 5, byte = (q & 31) * 4;
+    char *base = reinterpret_cast<char *>(tf32);
+    *reinterpret_cast<uint32_t *>(base + sw128_offset(t, byte, 2 * n2, chunk)) = hi;
+    *reinterpret_cast<uint32_t *>(base + sw128_offset(n2 + t, byte, 2 * n2, chunk)) = lo;
   }
 }
 
@@ -140,7 +181,8 @@ cudaError_t launch_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   build_m_kernel<<<n2, n2, 0, s>>>(op->n, op->f16_scale_exp, op->d_C64, op->d_G64, op->d_M64,
-                                   op->d_M32, op->d_Mdc, op->d_f16);
+                                   op->d_M32, op->d_Mdc, op->d_f16, op->d_bf16, op->d_tf32,
+                                   op->d_f16_pix, op->d_Gdc);
   return cudaGetLastError();
 }
 

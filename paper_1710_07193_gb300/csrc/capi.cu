@@ -103,7 +103,10 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   op->n = n; op->n2 = n * n;
   const size_t n2 = op->n2, sq = n2 * n2;
   const bool pieces = tc_supported(n, DCTF_F16X3);
-  size_t off = 0, o_C64, o_M64, o_H64, o_G64, o_M32, o_Mdc, o_f16 = 0, o_err;
+  const bool wide = n == 16;                  // BF16 and TF32 pieces too
+  const bool pix = n == 8;                    // pixel operator pieces too
+  size_t off = 0, o_C64, o_M64, o_H64, o_G64, o_M32, o_Mdc, o_f16 = 0, o_bf16 = 0, o_tf32 = 0,
+         o_pix = 0, o_gdc = 0, o_err;
   o_C64 = off; off = align_up(off + n2 * 8, 1024);
   o_M64 = off; off = align_up(off + sq * 8, 1024);
   o_H64 = off; off = align_up(off + sq * 8, 1024);
@@ -111,6 +114,14 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   o_M32 = off; off = align_up(off + sq * 4, 1024);
   o_Mdc = off; off = align_up(off + n2 * 4, 1024);
   if (pieces) { o_f16 = off; off = align_up(off + 2 * sq * 2, 1024); }
+  if (pix) {
+    o_pix = off; off = align_up(off + 2 * sq * 2, 1024);
+    o_gdc = off; off = align_up(off + n2 * 4, 1024);
+  }
+  if (wide) {
+    o_bf16 = off; off = align_up(off + 3 * sq * 2, 1024);
+    o_tf32 = off; off = align_up(off + 2 * sq * 4, 1024);
+  }
   o_err = off; off = align_up(off + 256, 1024);
   cudaError_t e = cudaMalloc(&op->d_base, off);
   if (e != cudaSuccess) { delete op; return cuda_error(e, "cudaMalloc(operator)"); }
@@ -123,6 +134,10 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   op->d_M32 = reinterpret_cast<float *>(b + o_M32);
   op->d_Mdc = reinterpret_cast<float *>(b + o_Mdc);
   op->d_f16 = pieces ? reinterpret_cast<__half *>(b + o_f16) : nullptr;
+  op->d_f16_pix = pix ? reinterpret_cast<__half *>(b + o_pix) : nullptr;
+  op->d_Gdc = pix ? reinterpret_cast<float *>(b + o_gdc) : nullptr;
+  op->d_bf16 = wide ? reinterpret_cast<__nv_bfloat16 *>(b + o_bf16) : nullptr;
+  op->d_tf32 = wide ? reinterpret_cast<uint32_t *>(b + o_tf32) : nullptr;
   op->d_err = reinterpret_cast<uint32_t *>(b + o_err);
   op->precision = pieces ? DCTF_F16X3 : DCTF_FP32_SIMT;
 
@@ -255,6 +270,41 @@ dctf_status dctf_apply(const dctf_operator *op, const float *coeffs, int64_t nbl
                              op->d_err, stream, (op->flags & DCTF_APPLY_INPUTS_READY) != 0);
   }
   if (e != cudaSuccess) return cuda_error(e, "dctf_apply launch");
+  return DCTF_OK;
+}
+
+dctf_status dctf_apply_pixels(const dctf_operator *op, const float *coeffs, int height,
+                              int width, uint8_t *image, int64_t pitch, dctf_stream_t stream) {
+  if (op == nullptr || coeffs == nullptr || image == nullptr)
+    return set_error(DCTF_EINVAL, "NULL argument");
+  if (op->n != 8 || op->d_f16_pix == nullptr)
+    return set_error(DCTF_EUNSUPPORTED, "the fused pixel apply needs an 8x8 operator");
+  if (height <= 0 || width <= 0 || height % 8 || width % 8)
+    return set_error(DCTF_EINVAL, "image %dx%d: sides must be positive multiples of 8", height,
+                     width);
+  if (pitch < width || pitch % 8)
+    return set_error(DCTF_EINVAL, "pitch %lld: must be >= width and a multiple of 8",
+                     (long long)pitch);
+  if (!aligned16(coeffs) || (reinterpret_cast<uintptr_t>(image) & 7))
+    return set_error(DCTF_EINVAL, "coeffs must be 16-byte and image 8-byte aligned");
+  const int64_t nblocks = (int64_t)(height / 8) * (width / 8);
+  const char *a = reinterpret_cast<const char *>(coeffs);
+  const char *b = reinterpret_cast<const char *>(image);
+  const size_t la = (size_t)nblocks * 64 * sizeof(float), lb = (size_t)(height - 1) * pitch + width;
+  if (a < b + lb && b < a + la) return set_error(DCTF_EINVAL, "coefficients and image overlap");
+  GroupItem gi;   // (its coefficient output map is not used: pointed at the input)
+  cudaError_t e = fill_group_item(&gi, op, coeffs, const_cast<float *>(coeffs), nblocks, false,
+                                  nullptr, nullptr);
+  if (e == cudaSuccess) {
+    gi.pieces = op->d_f16_pix;
+    gi.mdc = op->d_Gdc;
+    gi.img = image;
+    gi.pitch = pitch;
+    gi.bw = width / 8;
+    e = launch_apply_pixels(gi, (nblocks + 63) / 64, sm_count(op->device), op->d_err, stream,
+                            (op->flags & DCTF_APPLY_INPUTS_READY) != 0);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "dctf_apply_pixels launch");
   return DCTF_OK;
 }
 

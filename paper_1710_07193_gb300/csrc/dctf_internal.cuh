@@ -65,6 +65,10 @@ struct dctf_operator {
   float *d_M32;             // [n2][n2] FP32 copy of M
   float *d_Mdc;             // [n2] M[:, 0] in FP32
   __half *d_f16;            // F16X3 pieces: rows 0..n2-1 hi, n2..2n2-1 lo (sw128)
+  __half *d_f16_pix;        // n = 8: F16X3 pieces of the pixel operator G = H K^T
+  float *d_Gdc;             // n = 8: G[:, 0] in FP32
+  __nv_bfloat16 *d_bf16;    // n = 16: BF16X6 pieces m0, m1, m2 (3 n2 rows per 64-chunk)
+  uint32_t *d_tf32;         // n = 16: TF32 pieces hi, lo (2 n2 rows per 32-chunk)
   uint32_t *d_err;          // device status word
   // dctf_apply_host staging (lazily allocated): kHostPipes streams, each
   // with an input and an output chunk buffer
@@ -85,10 +89,11 @@ cudaError_t launch_apply_simt(const dctf_operator *op, const float *x,
                               const double *x64, int64_t nblocks, float *y,
                               cudaStream_t s);
 
-// tensor-core kernels exist for these (n, precision): apply_group.cu (n = 8)
-// and apply_n16.cu (n = 16)
+// tensor-core kernels exist for these (n, precision): apply_group.cu (n = 8,
+// F16X3) and apply_n16.cu (n = 16, every split precision)
 inline bool tc_supported(int n, dctf_precision p) {
-  return (n == 8 || n == 16) && p == DCTF_F16X3;
+  if (n == 8) return p == DCTF_F16X3;
+  return n == 16 && (p == DCTF_F16X3 || p == DCTF_BF16X6 || p == DCTF_TF32X1 || p == DCTF_TF32X3);
 }
 cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks,
                              float *y, cudaStream_t s);

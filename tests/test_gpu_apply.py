@@ -46,7 +46,15 @@ def check(y, x32, blocks, w, a, n, boundary, pixels=True):
 
 
 def precisions(n, dctf):
-    return [dctf.FP32_SIMT, dctf.F16X3] if n in (8, 16) else [dctf.FP32_SIMT]
+    """The variants held to the bar for block size n (TF32X1 is not: see
+    test_tf32x1_error_bound)."""
+    if n == 16:
+        return [dctf.FP32_SIMT, dctf.F16X3, dctf.BF16X6, dctf.TF32X3]
+    return [dctf.FP32_SIMT, dctf.F16X3] if n == 8 else [dctf.FP32_SIMT]
+
+
+def n16_tc(dctf):
+    return [dctf.F16X3, dctf.BF16X6, dctf.TF32X3, dctf.TF32X1]
 
 
 @pytest.fixture(scope="module")
@@ -143,9 +151,18 @@ def test_other_block_sizes(dctf, n):
             with pytest.raises(dctf.DctfError):
                 op.set_precision(dctf.F16X3)
         else:
-            op.set_precision(dctf.F16X3)
-            with pytest.raises(dctf.DctfError):
-                run(dctf, op, x, dctf.F16X3, inplace=True)
+            for p in n16_tc(dctf):
+                with pytest.raises(dctf.DctfError):
+                    run(dctf, op, x, p, inplace=True)
+
+
+def test_split_variants_need_16x16(dctf):
+    op = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 8, dctf.ZERO)
+    for p in (dctf.BF16X6, dctf.TF32X1, dctf.TF32X3):
+        with pytest.raises(dctf.DctfError) as e:
+            op.set_precision(p)
+        assert e.value.status == 6                          # EUNSUPPORTED
+    op.release()
 
 
 @pytest.mark.parametrize("prec", ["simt", "f16x3"])
@@ -225,18 +242,54 @@ def test_full_size_headline_sampled(dctf, headline_full):
     assert op.status() == 0
 
 
-@pytest.mark.parametrize("nb", [1, 127, 129, 1000, 40000])
-def test_n16_tensor_core_ragged(dctf, nb):
-    """16x16 blocks, perturbed 9x9 Gaussian, border replication: the
-    tensor-core kernel (output halves on CTA pairs, K-chunked input)."""
+@pytest.fixture(scope="module")
+def n16_source():
     img = datagen.synthetic_image(3200, 3200, datagen.rng(96, 0, 0))
     blocks, x = coeffs_of(img, 16)
-    x = x[:nb].astype(np.float32)
-    blocks = blocks[:nb]
+    return blocks, x.astype(np.float32)
+
+
+@pytest.mark.parametrize("nb", [1, 127, 129, 1000, 40000])
+@pytest.mark.parametrize("prec", ["F16X3", "BF16X6", "TF32X3"])
+def test_n16_tensor_core_ragged(dctf, n16_source, nb, prec):
+    """16x16 blocks, perturbed 9x9 Gaussian, border replication: the
+    tensor-core kernels (outputs split over 2 or 4 CTAs, K-chunked input)
+    on block counts that leave partial tiles and idle CTA groups."""
+    blocks, x = n16_source
+    x, blocks = x[:nb], blocks[:nb]
     w, a = datagen.large_mask(), (4, 4)
     op = dctf.build_operator(w, a, 16, dctf.REPLICATE)
-    check(run(dctf, op, x, dctf.F16X3), x, blocks, w, a, 16, oracle.REPLICATE)
+    check(run(dctf, op, x, getattr(dctf, prec)), x, blocks, w, a, 16, oracle.REPLICATE)
     assert op.status() == 0
+    op.release()
+
+
+def tf32x1_bound(m, x):
+    """Bound on |y - M x| for TF32X1 from its arithmetic: x_k and M_jk each
+    carry a relative rounding error <= 2^-11 (10 explicit mantissa bits,
+    round to nearest), so each product is off by <= (2^-10 + 2^-22)|M_jk x_k|;
+    the FP32 accumulation (32 chunked additions per accumulator, truncating)
+    adds <= 2^-18 sum_k |M_jk x_k|; the DC term is exact to FP32 rounding."""
+    s = np.abs(x[:, 1:]) @ np.abs(m[:, 1:]).T
+    return (2.0**-10 + 2.0**-17) * s + 1e-5 * (1 + np.abs(x[:, :1]) * np.abs(m[:, 0])[None, :])
+
+
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_tf32x1_error_bound(dctf, n16_source, boundary):
+    """TF32X1 is not exact; its error stays inside the bound its arithmetic
+    gives, and is far above the other splits' (so the variant is really
+    running at TF32 precision)."""
+    _, x = n16_source
+    x = x[:5000]
+    w, a = datagen.large_mask(), (4, 4)
+    op = dctf.build_operator(w, a, 16, boundary)
+    y = run(dctf, op, x, dctf.TF32X1)
+    m = oracle.build_M(w, a, 16, boundary)
+    y_ref = oracle.apply_M(m, x.astype(np.float64))
+    err = np.abs(y - y_ref)
+    assert (err <= tf32x1_bound(m, x.astype(np.float64))).all()
+    assert err.max() > 1e-2
+    op.release()
 
 
 def test_error_table_16x16(dctf, capsys):
@@ -249,8 +302,12 @@ def test_error_table_16x16(dctf, capsys):
     w, a = datagen.large_mask(), (4, 4)
     op = dctf.build_operator(w, a, 16, dctf.REPLICATE)
     errs = {}
-    for name, p in (("FP32_SIMT", dctf.FP32_SIMT), ("F16X3", dctf.F16X3)):
-        errs[name] = check(run(dctf, op, x, p), x, blocks, w, a, 16, oracle.REPLICATE)
+    for name in ("FP32_SIMT", "F16X3", "BF16X6", "TF32X3"):
+        errs[name] = check(run(dctf, op, x, getattr(dctf, name)), x, blocks, w, a, 16,
+                           oracle.REPLICATE)
+    y = run(dctf, op, x, dctf.TF32X1)
+    errs["TF32X1"] = np.abs(y - oracle.apply_M(oracle.build_M(w, a, 16, oracle.REPLICATE),
+                                               x.astype(np.float64))).max()
     with capsys.disabled():
         print(f"\n16x16 max coefficient error: {errs}")
 
