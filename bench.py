@@ -346,7 +346,7 @@ def run_workloads(lib, torch, reps: int):
     lib.forward_dct(img, 8192, 8192, 16, xl)
     del img
     yl = torch.empty_like(xl)
-    op = lib.build_operator(job.mask, job.anchor, 16, job.boundary)
+    op = lib.build_operator(job.mask, job.anchor, 16, job.boundary, kron=True)
     # error of each arithmetic against the operator's own FP64 M (built on
     # the device, equal to the paper's M to 1e-12) applied in FP64 on the
     # host to a sample of 4096 blocks spread over the image
@@ -355,12 +355,28 @@ def run_workloads(lib, torch, reps: int):
     xs64 = xl[idx.to(dev)].double().cpu().numpy()
     ys64 = xs64 @ m64.T
     res = {"blocks": nb, "error_sample_blocks": 4096}
-    for name in ("F16X3", "BF16X6", "TF32X3", "TF32X1", "FP32_SIMT"):
+    for name in ("F16X3", "BF16X6", "TF32X3", "TF32X1", "FP32_SIMT", "KRON_FP32"):
         op.set_precision(getattr(lib, name))
         t = graph_time_ms(torch, lambda s: lib.apply(op, xl, nb, yl, stream=s), max(1, reps // 4))
         err = float(abs(yl[idx.to(dev)].double().cpu().numpy() - ys64).max())
         res[name] = {"us": 1e3 * t, "blocks_per_s": nb / (t / 1e3),
                      "GBps": nb * 2048 / (t / 1e3) / 1e9, "max_coef_err_vs_fp64": err}
+    res["KRON_FP32"]["terms"] = op.kron_rank()
+    op.release()
+    # the paper form's best case: a separable mask (the workload's 9x9
+    # Gaussian without its perturbation, one Kronecker term)
+    sep = datagen.gaussian_mask(9, 2.5)
+    op = lib.build_operator(sep, job.anchor, 16, job.boundary, kron=True)
+    m64, _ = op.download()
+    ys64 = xl[idx.to(dev)].double().cpu().numpy() @ m64.T
+    for name in ("KRON_FP32", "F16X3"):
+        op.set_precision(getattr(lib, name))
+        t = graph_time_ms(torch, lambda s: lib.apply(op, xl, nb, yl, stream=s), max(1, reps // 4))
+        err = float(abs(yl[idx.to(dev)].double().cpu().numpy() - ys64).max())
+        res[f"separable_9x9_{name}"] = {"us": 1e3 * t, "blocks_per_s": nb / (t / 1e3),
+                                        "GBps": nb * 2048 / (t / 1e3) / 1e9,
+                                        "max_coef_err_vs_fp64": err}
+    res["separable_9x9_KRON_FP32"]["terms"] = op.kron_rank()
     out["large_8192x8192_16x16"] = res
     op.release()
     return out
@@ -519,6 +535,33 @@ def run_dctf(args):
                     "bytes_per_block": PIXEL_BYTES_PER_BLOCK,
                     "kernel": "apply_group_kernel<float,4,1,false,true> (pixel epilogue)"}
     del imgs
+    # image-plane coefficient layout (dctf_apply_planar): the same
+    # coefficients rearranged as an h x w plane, 512 B per block
+    pl_in = [x.view(h // 8, w // 8, 8, 8).permute(0, 2, 1, 3).reshape(h, w).contiguous()
+             for x in xs[:4]]
+    pl_out = [torch.empty_like(pl_in[0]) for _ in range(4)]
+
+    def planar_graph(steps):
+        main = torch.cuda.Stream()
+        lib.apply_planar(ops[0], pl_in[0], h, w, pl_out[0], stream=main)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=main, capture_error_mode="thread_local"):
+            for i in range(steps):
+                lib.apply_planar(ops[0], pl_in[i % 4], h, w, pl_out[i % 4], stream=main)
+        torch.cuda.synchronize()
+        return g
+
+    planar_graph(max(args.warmup, 1)).replay()
+    pl_ms, _ = run_timed(planar_graph(px_steps))
+    pl_us = 1e3 * pl_ms / px_steps
+    pl_gbps = BYTES_PER_BLOCK * nb / (pl_us / 1e6) / 1e9
+    planar = {"us": pl_us, "blocks_per_s": ws * nb / (pl_us / 1e6), "GBps": pl_gbps,
+              "frac_of_measured_hbm": pl_gbps / measured_peaks()[0],
+              "layout": "h x w FP32 plane, coefficient (u,v) of block (by,bx) at (8by+u, 8bx+v); "
+                        "4 rotating plane pairs (537 MB > L2)",
+              "kernel": "apply_group_kernel<float,4,1,false,2> (4-D TMA boxes)"}
+    del pl_in, pl_out
     op = ops[0]
     op.set_precision(lib.F16X3)
     # the operator build alone (2 kernels), for the record
@@ -584,6 +627,7 @@ def run_dctf(args):
                      "timing": "events around K back-to-back applies in one CUDA graph"},
         "fp32_simt": simt,
         "fused_pixels": fused_pixels,
+        "planar_layout": planar,
         "e2e": e2e,
         "serving": serving,
         "workloads": workloads,

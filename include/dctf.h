@@ -73,6 +73,12 @@ typedef enum { DCTF_ZERO = 0, DCTF_REPLICATE = 1 } dctf_boundary;
  *  TF32X1    : tcgen05, x and M rounded to TF32 once, one product; about
  *              3 decimal digits, NOT within the 1e-3 coefficient bar (for
  *              comparison).  n = 16.
+ *  KRON_FP32 : the paper's form (Sec. II.B Eq. 11-12, Sec. II.C Eq. 20):
+ *              M = sum_t A_t kron B_t with one term per rank of the mask,
+ *              applied as sandwich products Y = sum_t A_t X B_t^T in FP32
+ *              on CUDA cores; r * 2 n^3 multiply-adds per block instead of
+ *              n^4 (8x fewer for a separable mask at n = 16).  Needs an
+ *              operator built with DCTF_BUILD_KRON; n = 4, 8, 16.
  * The tensor-core variants of 16x16 blocks do not run in place.
  * dctf_operator_set_precision returns DCTF_EUNSUPPORTED for a variant that
  * has no kernel for the operator's n. */
@@ -81,7 +87,8 @@ typedef enum {
     DCTF_F16X3 = 1,
     DCTF_BF16X6 = 2,
     DCTF_TF32X1 = 3,
-    DCTF_TF32X3 = 4
+    DCTF_TF32X3 = 4,
+    DCTF_KRON_FP32 = 5
 } dctf_precision;
 
 typedef struct dctf_operator dctf_operator;
@@ -105,6 +112,12 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw,
  * (the other natural reading of Eq. 5), i.e. a correlation with the mask
  * rotated by 180 degrees and the anchor mirrored to (mh-1-ar, mw-1-ac). */
 enum { DCTF_MASK_CONVOLUTION = 1u };
+/* DCTF_BUILD_KRON: also keep the operator's Kronecker factors (every
+ * rebuild recomputes them): the host splits the mask into rank(w) separable
+ * terms by Gaussian elimination with complete pivoting (terms below 1e-13 of
+ * the largest entry are dropped), and the device forms the DCT-domain 1-D
+ * filters of each term in FP64 (stored FP32).  Enables DCTF_KRON_FP32. */
+enum { DCTF_BUILD_KRON = 2u };
 dctf_status dctf_build_operator_ex(const double *mask, int mh, int mw,
                                    const int anchor[2], int n,
                                    dctf_boundary boundary, uint32_t flags,
@@ -149,6 +162,11 @@ dctf_status dctf_operator_download(const dctf_operator *op, double *M_host,
  * clear != 0 the word is reset to 0 afterwards. */
 dctf_status dctf_operator_status(dctf_operator *op, uint32_t *code, int clear);
 
+/* Number of Kronecker terms of an operator built with DCTF_BUILD_KRON (the
+ * numerical rank of its mask; 0 for an all-zero mask).  EUNSUPPORTED for an
+ * operator built without the flag.  Host only, no synchronisation. */
+dctf_status dctf_operator_kron_rank(const dctf_operator *op, int *rank);
+
 void dctf_release_operator(dctf_operator *op);
 
 /* y_b = M x_b for b < nblocks (Eq. 11 zero padding, Eq. 20 replication).
@@ -176,6 +194,21 @@ dctf_status dctf_apply(const dctf_operator *op, const float *coeffs,
 dctf_status dctf_apply_pixels(const dctf_operator *op, const float *coeffs,
                               int height, int width, uint8_t *image,
                               int64_t pitch, dctf_stream_t stream);
+
+/* dctf_apply for coefficients in the image-plane layout (a JPEG decoder's
+ * coefficient plane): an FP32 array shaped like the pixel image, where
+ * coefficient (u, v) of block (by, bx) sits at row 8 by + u, column 8 bx + v.
+ * The kernel reads and writes it with 4-D TMA boxes (no layout conversion
+ * pass).  Same arithmetic as dctf_apply (F16X3 tensor cores).
+ *  coeffs, out  device FP32, height rows of pitch / out_pitch floats
+ *               (pitches >= width, multiples of 4; 16-byte aligned); only
+ *               the height x width coefficients are written.  out == coeffs
+ *               (in place, equal pitches) allowed; no other overlap.
+ * 8x8 operators only (EUNSUPPORTED otherwise); honours
+ * DCTF_APPLY_INPUTS_READY.  Asynchronous on `stream`. */
+dctf_status dctf_apply_planar(const dctf_operator *op, const float *coeffs,
+                              int height, int width, int64_t pitch, float *out,
+                              int64_t out_pitch, dctf_stream_t stream);
 
 /* As dctf_apply, with FP64 input coefficients (FP32 output), FP32 SIMT
  * arithmetic; for the small FP64-coefficient workload. */

@@ -30,6 +30,7 @@ __all__ = [
     "kron_dct", "build_M", "apply_M", "round_half_away", "to_uint8",
     "dequantise", "requantise", "serve_blocks", "pixel_route",
     "coefficient_route", "uint8_compare", "int16_compare",
+    "mask_rank_terms", "filter_1d", "kron_factors", "apply_kron",
 ]
 
 ZERO, REPLICATE = 0, 1
@@ -165,6 +166,63 @@ def build_M(w: np.ndarray, anchor, n: int, boundary: int) -> np.ndarray:
     """
     k = kron_dct(n)
     return k @ build_H(w, anchor, n, boundary) @ k.T
+
+
+# ------------------------------------ Sec. II.B-C, Eq. 11 / Eq. 20 (Kronecker form)
+def mask_rank_terms(w: np.ndarray, rel_tol: float = 1e-13):
+    """w = sum_t u_t v_t^T with as few terms as the mask's rank (its SVD;
+    terms whose singular value is below rel_tol * the largest are dropped)."""
+    w = np.asarray(w, dtype=np.float64)
+    u, s, vt = np.linalg.svd(w)
+    if s.size == 0 or s[0] == 0.0:
+        return []
+    return [(s[t] * u[:, t], vt[t, :]) for t in range(s.size) if s[t] > rel_tol * s[0]]
+
+
+def filter_1d(v: np.ndarray, a: int, n: int, boundary: int) -> np.ndarray:
+    """n x n matrix of the 1-D correlation along one axis of a block:
+    out[i] = sum_r v[r] x(i + r - a), x outside [0, n) zero (Sec. II.B) or
+    the nearest end value (Sec. II.C)."""
+    h = np.zeros((n, n), dtype=np.float64)
+    for i in range(n):
+        for r in range(len(v)):
+            s = i + r - a
+            if boundary == ZERO:
+                if 0 <= s < n:
+                    h[i, s] += v[r]
+            else:
+                h[i, min(max(s, 0), n - 1)] += v[r]
+    return h
+
+
+def kron_factors(w: np.ndarray, anchor, n: int, boundary: int):
+    """M = sum_t A_t kron B_t, the form of Eq. 11 (three Kronecker terms for a
+    3x3 mask) for any mask.
+
+    A separable mask u v^T filters along the block's rows and columns
+    independently, and both paddings act on each axis on its own (a pixel is
+    dropped when either coordinate leaves the block; replication clamps
+    each coordinate), so its H is the Kronecker product of the two 1-D
+    operators.  Writing w as a sum of rank-1 terms and conjugating by C
+    (Eq. 7) gives A_t = C H_u C^T, B_t = C H_v C^T; vec(A X B^T) =
+    (A kron B) vec(X) for the row-major vec.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    _check_mask(w, anchor, n, boundary)
+    ar, ac = anchor
+    c = dct_matrix(n)
+    return [(c @ filter_1d(u, ar, n, boundary) @ c.T, c @ filter_1d(v, ac, n, boundary) @ c.T)
+            for u, v in mask_rank_terms(w)]
+
+
+def apply_kron(factors, coeffs: np.ndarray, n: int) -> np.ndarray:
+    """y_b = sum_t vec(A_t X_b B_t^T) for every block: the sandwich products
+    of Eq. 11 / Eq. 12; [nb, n*n] float64."""
+    x = np.asarray(coeffs, dtype=np.float64).reshape(-1, n, n)
+    y = np.zeros_like(x)
+    for a, b in factors:
+        y += np.einsum("ik,bkl,jl->bij", a, x, b)
+    return y.reshape(-1, n * n)
 
 
 def apply_M(m: np.ndarray, coeffs: np.ndarray) -> np.ndarray:

@@ -14,17 +14,17 @@ import os
 import numpy as np
 
 __all__ = [
-    "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3",
+    "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3", "KRON_FP32",
     "DctfError", "load", "lib_path", "exported_symbols", "build_operator", "Operator",
-    "apply", "apply_f64in", "apply_host", "apply_pixels", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
+    "apply", "apply_f64in", "apply_host", "apply_pixels", "apply_planar", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
     "version", "IO_F32", "IO_I16", "Group", "group_create", "apply_grouped", "Server",
 ]
 
 ZERO, REPLICATE = 0, 1
 IO_F32, IO_I16 = 0, 1
 APPLY_INPUTS_READY = 1
-MASK_CONVOLUTION = 1
-FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3 = 0, 1, 2, 3, 4
+MASK_CONVOLUTION, BUILD_KRON = 1, 2
+FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3, KRON_FP32 = 0, 1, 2, 3, 4, 5
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ETIMEOUT",
            6: "EUNSUPPORTED"}
 
@@ -40,12 +40,14 @@ _SIGS = {
     "dctf_operator_rebuild": (_i32, [_vp, _vp, _i32, _i32, _vp, _i32, _vp]),
     "dctf_operator_set_precision": (_i32, [_vp, _i32]),
     "dctf_operator_set_flags": (_i32, [_vp, _u32]),
+    "dctf_operator_kron_rank": (_i32, [_vp, _vp]),
     "dctf_operator_download": (_i32, [_vp, _vp, _vp]),
     "dctf_operator_status": (_i32, [_vp, _vp, _i32]),
     "dctf_release_operator": (None, [_vp]),
     "dctf_apply": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "dctf_apply_f64in": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "dctf_apply_pixels": (_i32, [_vp, _vp, _i32, _i32, _vp, _i64, _vp]),
+    "dctf_apply_planar": (_i32, [_vp, _vp, _i32, _i32, _i64, _vp, _i64, _vp]),
     "dctf_apply_host": (_i32, [_vp, _vp, _i64, _vp]),
     "dctf_forward_dct": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
     "dctf_forward_dct_f64": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
@@ -149,6 +151,12 @@ class Operator:
     def set_flags(self, flags: int) -> None:
         _check(load().dctf_operator_set_flags(self.handle, flags))
 
+    def kron_rank(self) -> int:
+        """Number of Kronecker terms (operators built with kron=True)."""
+        r = ctypes.c_int(0)
+        _check(load().dctf_operator_kron_rank(self.handle, ctypes.addressof(r)))
+        return r.value
+
     def download(self) -> tuple[np.ndarray, np.ndarray]:
         m = np.empty((self.n2, self.n2), dtype=np.float64)
         h = np.empty((self.n2, self.n2), dtype=np.float64)
@@ -173,7 +181,7 @@ class Operator:
 
 
 def build_operator(mask, anchor, n: int, boundary: int, stream=None,
-                   convolution: bool = False) -> Operator:
+                   convolution: bool = False, kron: bool = False) -> Operator:
     m = np.ascontiguousarray(mask, dtype=np.float64)
     if m.ndim != 2:
         raise ValueError("mask must be 2-D")
@@ -181,7 +189,8 @@ def build_operator(mask, anchor, n: int, boundary: int, stream=None,
     h = ctypes.c_void_p(0)
     _check(load().dctf_build_operator_ex(m.ctypes.data, m.shape[0], m.shape[1],
                                          ctypes.addressof(a), n, boundary,
-                                         MASK_CONVOLUTION if convolution else 0,
+                                         (MASK_CONVOLUTION if convolution else 0)
+                                         | (BUILD_KRON if kron else 0),
                                          _stream(stream), ctypes.addressof(h)))
     return Operator(h.value, n)
 
@@ -197,6 +206,14 @@ def apply_pixels(op: Operator, coeffs, height: int, width: int, image,
     height rows of `pitch` bytes), one fused pass (8x8 operators)."""
     _check(load().dctf_apply_pixels(op.handle, _ptr(coeffs), height, width, _ptr(image),
                                     pitch or width, _stream(stream)))
+
+
+def apply_planar(op: Operator, coeffs, height: int, width: int, out, pitch: int | None = None,
+                 out_pitch: int | None = None, stream=None) -> None:
+    """Image-plane coefficients (device FP32, coefficient (u, v) of block
+    (by, bx) at row 8 by + u, column 8 bx + v) -> the same layout, filtered."""
+    _check(load().dctf_apply_planar(op.handle, _ptr(coeffs), height, width, pitch or width,
+                                    _ptr(out), out_pitch or pitch or width, _stream(stream)))
 
 
 def apply_f64in(op: Operator, coeffs, nblocks: int, out, stream=None) -> None:

@@ -28,12 +28,19 @@
 //  * Quantised I/O (IoT = int16_t): the converter dequantises x = Q q_in
 //    before the split, the epilogue requantises round_half_away(y / q_out)
 //    with int16 saturation, so int16 coefficients go HBM -> HBM directly.
-//  * Pixel output (kPix): the operator is G = H K^T, which takes a block's
+//  * Pixel output (kMode = kModePixels): the operator is G = H K^T, which takes a block's
 //    DCT coefficients straight to its filtered pixels (K^T K = I, so
 //    K^T M = H K^T, Eq. 3 applied after Eq. 7); the epilogue rounds half
 //    away from zero, saturates to [0, 255] and writes the block's 8 x 8
 //    bytes into the image (Sec. III's conversion), 64 B per block instead
 //    of 256 B of coefficients.
+//  * Image-plane layout (kMode = kModePlanar): the coefficients of block
+//    (by, bx) sit at rows 8 by + u, columns 8 bx + v of an image-shaped FP32
+//    array (the layout of a JPEG decoder's coefficient plane).  A 4-D TMA
+//    view (v, bx, u, by) loads a tile of 128 blocks of one block row as one
+//    box and stores 32 blocks per epilogue warp the same way; block rows
+//    are padded to a multiple of 128 blocks in the tile walk (the padding
+//    is outside the tensor: zero-filled on load, clipped on store).
 //
 // Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM
 // allocator, warp 3 slot loader, warps 4-7 converter (thread = tile row),
@@ -208,7 +215,9 @@ struct TileWalk {
 // FP32 I/O: at most 152 registers a thread (58,368 of the SM's 65,536 for 384
 // threads), so the small FP64 operator-build kernels of the next image can
 // run on the same SMs while this kernel streams.
-template <typename IoT, int S, int NS, bool kGroup, bool kPix>
+enum : int { kModeBlocks = 0, kModePixels = 1, kModePlanar = 2 };
+
+template <typename IoT, int S, int NS, bool kGroup, int kMode>
 __global__ void __maxnreg__(sizeof(IoT) == 4 ? 152 : 168)
 apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__ GroupItem single,
                    int nitems, int64_t total_halves, int max_take, int interleaved,
@@ -270,9 +279,15 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       const void *map = t.rows == kTile ? (const void *)&gi.tm_in : (const void *)&gi.tm_in_half;
       mbar_arrive_expect_tx(&full_in[s], t.rows * Io<IoT>::kRowBytes);
       uint8_t *dst = s_in + s * L::kStageBytes;
+      if constexpr (kMode == kModePlanar) {
+        // box (v 8, bx t.rows, u 8, by 1) -> shared [u][t.rows][v]
+        const int by = t.row0 / (int)gi.bw, bx0 = t.row0 % (int)gi.bw;
+        tma_load_4d(map, &full_in[s], dst, 0, bx0, 0, by);
+      } else {
 #pragma unroll
-      for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
-        tma_load_2d(map, &full_in[s], dst + bx * L::kBoxBytes, bx * Io<IoT>::kBoxCols, t.row0);
+        for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
+          tma_load_2d(map, &full_in[s], dst + bx * L::kBoxBytes, bx * Io<IoT>::kBoxCols, t.row0);
+      }
       ++issued;
       ++it;
     }
@@ -353,7 +368,17 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       if (!warp_wait_bounded(&full_in[s], ps, s_abort, err, kRoleConv | (it << 8))) break;
       float v[64];
       const uint8_t *st = s_in + s * L::kStageBytes + row * 128;
-      if constexpr (Io<IoT>::kBoxesPerRow == 2) {
+      if constexpr (kMode == kModePlanar) {
+        // shared [u][t.rows][v]: this block's row u is 32 bytes at (u t.rows + row) * 32
+        const uint8_t *sp = s_in + s * L::kStageBytes;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 *q = reinterpret_cast<const float4 *>(sp + (u * t.rows + row) * 32);
+          const float4 a = q[0], b = q[1];
+          v[8 * u] = a.x; v[8 * u + 1] = a.y; v[8 * u + 2] = a.z; v[8 * u + 3] = a.w;
+          v[8 * u + 4] = b.x; v[8 * u + 5] = b.y; v[8 * u + 6] = b.z; v[8 * u + 7] = b.w;
+        }
+      } else if constexpr (Io<IoT>::kBoxesPerRow == 2) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const float4 q = *reinterpret_cast<const float4 *>(
@@ -455,7 +480,7 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         acc[4 * u + 2] = fmaf(acc[4 * u + 2], out_scale, md.z * x0);
         acc[4 * u + 3] = fmaf(acc[4 * u + 3], out_scale, md.w * x0);
       }
-      if constexpr (kPix) {
+      if constexpr (kMode == kModePixels) {
         // block b of the item covers image rows 8 (b / bw) + 0..7 and columns
         // 8 (b % bw) + 0..7; its pixel (i, j) is output i * 8 + j.  The lanes
         // of a warp hold consecutive blocks, so each row's 8-byte stores of a
@@ -488,7 +513,15 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       if (lane == 0) bulk_wait_read<1>();             // slab o free (store of tile it-2 read it)
       __syncwarp();
       uint8_t *slab = s_out + o * L::kStageBytes + wr * L::kSlabBytes;
-      if constexpr (Io<IoT>::kBoxesPerRow == 2) {
+      if constexpr (kMode == kModePlanar) {
+        // shared [u][32][v] for this warp's 32 blocks
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float4 *q = reinterpret_cast<float4 *>(slab + (u * 32 + r32) * 32);
+          q[0] = make_float4(acc[8 * u], acc[8 * u + 1], acc[8 * u + 2], acc[8 * u + 3]);
+          q[1] = make_float4(acc[8 * u + 4], acc[8 * u + 5], acc[8 * u + 6], acc[8 * u + 7]);
+        }
+      } else if constexpr (Io<IoT>::kBoxesPerRow == 2) {
 #pragma unroll
         for (int u = 0; u < 16; ++u)
           *reinterpret_cast<float4 *>(slab + (u >> 3) * L::kSlabBoxBytes + r32 * 128 +
@@ -521,9 +554,13 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       if (lane == 0) {
         if (store) {
           const int y0 = t.row0 + wr * 32;
+          if constexpr (kMode == kModePlanar) {
+            tma_store_4d(&gi.tm_out, slab, 0, y0 % (int)gi.bw, 0, y0 / (int)gi.bw);
+          } else {
 #pragma unroll
-          for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
-            tma_store_2d(&gi.tm_out, slab + bx * L::kSlabBoxBytes, bx * Io<IoT>::kBoxCols, y0);
+            for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
+              tma_store_2d(&gi.tm_out, slab + bx * L::kSlabBoxBytes, bx * Io<IoT>::kBoxCols, y0);
+          }
         }
         bulk_commit();
       }
@@ -577,11 +614,11 @@ cudaError_t make_map(CUtensorMap *m, const void *ptr, int64_t nblocks, bool i16,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <typename IoT, int S, int NS, bool kGroup, bool kPix = false>
+template <typename IoT, int S, int NS, bool kGroup, int kMode = kModeBlocks>
 cudaError_t launch_cfg(const GroupItem *d_items, const GroupItem &single, int nitems,
                        int64_t total_halves, int grid, int max_take, int interleaved,
                        uint32_t *err, cudaStream_t s, bool pdl) {
-  auto kern = apply_group_kernel<IoT, S, NS, kGroup, kPix>;
+  auto kern = apply_group_kernel<IoT, S, NS, kGroup, kMode>;
   constexpr int smem = Layout<IoT, S, NS>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -628,8 +665,47 @@ cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, i
   int64_t g = grid > 0 ? grid : 0;
   if (g > total_halves) g = total_halves;
   if (g < 1) g = 1;
-  return launch_cfg<float, 4, 1, false, true>(nullptr, single, 1, total_halves, (int)g, 2, 1, err,
-                                              s, pdl);
+  return launch_cfg<float, 4, 1, false, kModePixels>(nullptr, single, 1, total_halves, (int)g, 2,
+                                                     1, err, s, pdl);
+}
+
+// Image-plane coefficients: the 4-D view (v, bx, u, by) of an FP32 array of
+// `height` rows of `pitch` floats; boxes of (8, box_blocks, 8, 1).
+static cudaError_t make_planar_map(CUtensorMap *m, const void *ptr, int height, int width,
+                                   int64_t pitch, int box_blocks) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return cudaErrorNotSupported;
+  cuuint64_t dims[4] = {8, (cuuint64_t)(width / 8), 8, (cuuint64_t)(height / 8)};
+  cuuint64_t strides[3] = {32, (cuuint64_t)pitch * 4, (cuuint64_t)pitch * 32};
+  cuuint32_t box[4] = {8, (cuuint32_t)box_blocks, 8, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(ptr), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int height, int width,
+                                int64_t in_pitch, float *out, int64_t out_pitch, uint32_t *err,
+                                cudaStream_t s, bool pdl) {
+  GroupItem gi;
+  memset(&gi, 0, sizeof gi);
+  cudaError_t e = make_planar_map(&gi.tm_in, in, height, width, in_pitch, kTile);
+  if (e == cudaSuccess) e = make_planar_map(&gi.tm_in_half, in, height, width, in_pitch, kHalf);
+  if (e == cudaSuccess) e = make_planar_map(&gi.tm_out, out, height, width, out_pitch, 32);
+  if (e != cudaSuccess) return e;
+  const int64_t bw_pad = (width / 8 + kTile - 1) / kTile * kTile;
+  gi.pieces = op->d_f16;
+  gi.mdc = op->d_Mdc;
+  gi.out_scale = ldexpf(1.0f, -op->f16_scale_exp);
+  gi.bw = bw_pad;
+  gi.nblocks = (int64_t)(height / 8) * bw_pad;      // tile walk over padded block rows
+  const int64_t total_halves = gi.nblocks / kHalf;
+  int64_t g = sm_count(op->device);
+  if (g > total_halves) g = total_halves;
+  if (g < 1) g = 1;
+  return launch_cfg<float, 4, 1, false, kModePlanar>(nullptr, gi, 1, total_halves, (int)g, 2, 1,
+                                                     err, s, pdl);
 }
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,

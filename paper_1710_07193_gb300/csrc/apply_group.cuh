@@ -44,6 +44,13 @@ cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *
 cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, int grid,
                                 uint32_t *err, cudaStream_t s, bool pdl);
 
+// Image-plane coefficient layout (8x8 blocks, F16X3): in/out are FP32
+// arrays of `height` rows of `pitch` floats, block (by, bx)'s coefficient
+// (u, v) at row 8 by + u, column 8 bx + v.
+cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int height, int width,
+                                int64_t in_pitch, float *out, int64_t out_pitch, uint32_t *err,
+                                cudaStream_t s, bool pdl);
+
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,
                                uint32_t *err, cudaStream_t s, bool pdl = false);

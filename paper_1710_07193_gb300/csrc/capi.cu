@@ -88,9 +88,9 @@ int dctf_version(void) { return 100; }
 
 const char *dctf_last_error(void) { return g_last_error.c_str(); }
 
-dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int anchor[2],
-                                int n, dctf_boundary boundary, dctf_stream_t stream,
-                                dctf_operator **out) {
+static dctf_status build_operator(const double *mask, int mh, int mw, const int anchor[2], int n,
+                                  dctf_boundary boundary, bool kron, dctf_stream_t stream,
+                                  dctf_operator **out) {
   if (out == nullptr) return set_error(DCTF_EINVAL, "out must not be NULL");
   *out = nullptr;
   MaskParams mp;
@@ -106,7 +106,7 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   const bool wide = n == 16;                  // BF16 and TF32 pieces too
   const bool pix = n == 8;                    // pixel operator pieces too
   size_t off = 0, o_C64, o_M64, o_H64, o_G64, o_M32, o_Mdc, o_f16 = 0, o_bf16 = 0, o_tf32 = 0,
-         o_pix = 0, o_gdc = 0, o_err;
+         o_pix = 0, o_gdc = 0, o_kA = 0, o_kB = 0, o_err;
   o_C64 = off; off = align_up(off + n2 * 8, 1024);
   o_M64 = off; off = align_up(off + sq * 8, 1024);
   o_H64 = off; off = align_up(off + sq * 8, 1024);
@@ -121,6 +121,10 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   if (wide) {
     o_bf16 = off; off = align_up(off + 3 * sq * 2, 1024);
     o_tf32 = off; off = align_up(off + 2 * sq * 4, 1024);
+  }
+  if (kron) {
+    o_kA = off; off = align_up(off + (size_t)kMaxN * n2 * 4, 1024);
+    o_kB = off; off = align_up(off + (size_t)kMaxN * n2 * 4, 1024);
   }
   o_err = off; off = align_up(off + 256, 1024);
   cudaError_t e = cudaMalloc(&op->d_base, off);
@@ -138,6 +142,9 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   op->d_Gdc = pix ? reinterpret_cast<float *>(b + o_gdc) : nullptr;
   op->d_bf16 = wide ? reinterpret_cast<__nv_bfloat16 *>(b + o_bf16) : nullptr;
   op->d_tf32 = wide ? reinterpret_cast<uint32_t *>(b + o_tf32) : nullptr;
+  op->kron = kron;
+  op->d_kA = kron ? reinterpret_cast<float *>(b + o_kA) : nullptr;
+  op->d_kB = kron ? reinterpret_cast<float *>(b + o_kB) : nullptr;
   op->d_err = reinterpret_cast<uint32_t *>(b + o_err);
   op->precision = pieces ? DCTF_F16X3 : DCTF_FP32_SIMT;
 
@@ -151,12 +158,20 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int an
   return DCTF_OK;
 }
 
+dctf_status dctf_build_operator(const double *mask, int mh, int mw, const int anchor[2],
+                                int n, dctf_boundary boundary, dctf_stream_t stream,
+                                dctf_operator **out) {
+  return build_operator(mask, mh, mw, anchor, n, boundary, false, stream, out);
+}
+
 dctf_status dctf_build_operator_ex(const double *mask, int mh, int mw, const int anchor[2], int n,
                                    dctf_boundary boundary, uint32_t flags, dctf_stream_t stream,
                                    dctf_operator **out) {
-  if (flags & ~(uint32_t)DCTF_MASK_CONVOLUTION) return set_error(DCTF_EINVAL, "unknown flags");
+  if (flags & ~(uint32_t)(DCTF_MASK_CONVOLUTION | DCTF_BUILD_KRON))
+    return set_error(DCTF_EINVAL, "unknown flags");
+  const bool kron = (flags & DCTF_BUILD_KRON) != 0;
   if (!(flags & DCTF_MASK_CONVOLUTION))
-    return dctf_build_operator(mask, mh, mw, anchor, n, boundary, stream, out);
+    return build_operator(mask, mh, mw, anchor, n, boundary, kron, stream, out);
   // convolution with w, anchor a = correlation with w rotated by 180 degrees
   // and the anchor mirrored: (mh - 1 - ar, mw - 1 - ac)
   if (mask == nullptr || anchor == nullptr || mh < 1 || mw < 1 || mh > kMaxN || mw > kMaxN)
@@ -165,7 +180,7 @@ dctf_status dctf_build_operator_ex(const double *mask, int mh, int mw, const int
   for (int r = 0; r < mh; ++r)
     for (int c = 0; c < mw; ++c) rot[(mh - 1 - r) * mw + (mw - 1 - c)] = mask[r * mw + c];
   const int a2[2] = {mh - 1 - anchor[0], mw - 1 - anchor[1]};
-  return dctf_build_operator(rot, mh, mw, a2, n, boundary, stream, out);
+  return build_operator(rot, mh, mw, a2, n, boundary, kron, stream, out);
 }
 
 dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask, int mh, int mw,
@@ -179,6 +194,7 @@ dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask, int mh,
   op->boundary = boundary;
   op->f16_scale_exp = f16_scale_exponent(mp);
   cudaError_t e = launch_build(op, mp, stream);
+  if (e == cudaSuccess && op->kron) e = launch_kron_build(op, mp, stream);
   if (e != cudaSuccess) return cuda_error(e, "operator build launch");
   return DCTF_OK;
 }
@@ -186,6 +202,13 @@ dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask, int mh,
 dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p) {
   if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
   if (p == DCTF_FP32_SIMT) { op->precision = p; return DCTF_OK; }
+  if (p == DCTF_KRON_FP32) {
+    if (!op->kron)
+      return set_error(DCTF_EUNSUPPORTED, "DCTF_KRON_FP32 needs an operator built with "
+                                          "DCTF_BUILD_KRON");
+    op->precision = p;
+    return DCTF_OK;
+  }
   if (p < DCTF_FP32_SIMT || p > DCTF_TF32X3)
     return set_error(DCTF_EINVAL, "unknown precision %d", (int)p);
   if (!tc_supported(op->n, p))
@@ -198,6 +221,13 @@ dctf_status dctf_operator_set_flags(dctf_operator *op, uint32_t flags) {
   if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
   if (flags & ~(uint32_t)DCTF_APPLY_INPUTS_READY) return set_error(DCTF_EINVAL, "unknown flags");
   op->flags = flags;
+  return DCTF_OK;
+}
+
+dctf_status dctf_operator_kron_rank(const dctf_operator *op, int *rank) {
+  if (op == nullptr || rank == nullptr) return set_error(DCTF_EINVAL, "NULL argument");
+  if (!op->kron) return set_error(DCTF_EUNSUPPORTED, "operator built without DCTF_BUILD_KRON");
+  *rank = op->krank;
   return DCTF_OK;
 }
 
@@ -256,6 +286,9 @@ dctf_status dctf_apply(const dctf_operator *op, const float *coeffs, int64_t nbl
   cudaError_t e;
   if (op->precision == DCTF_FP32_SIMT) {
     e = launch_apply_simt(op, coeffs, nullptr, nblocks, out, stream);
+  } else if (op->precision == DCTF_KRON_FP32) {
+    e = launch_apply_kron(op, coeffs, nblocks, out, stream);   // in place is fine: a thread
+                                                               // writes only the row it read
   } else if (op->n == 16) {
     if (static_cast<const void *>(coeffs) == static_cast<const void *>(out))
       return set_error(DCTF_EINVAL,
@@ -305,6 +338,34 @@ dctf_status dctf_apply_pixels(const dctf_operator *op, const float *coeffs, int 
                             (op->flags & DCTF_APPLY_INPUTS_READY) != 0);
   }
   if (e != cudaSuccess) return cuda_error(e, "dctf_apply_pixels launch");
+  return DCTF_OK;
+}
+
+dctf_status dctf_apply_planar(const dctf_operator *op, const float *coeffs, int height, int width,
+                              int64_t pitch, float *out, int64_t out_pitch,
+                              dctf_stream_t stream) {
+  if (op == nullptr || coeffs == nullptr || out == nullptr)
+    return set_error(DCTF_EINVAL, "NULL argument");
+  if (op->n != 8 || op->d_f16 == nullptr)
+    return set_error(DCTF_EUNSUPPORTED, "the image-plane apply needs an 8x8 operator");
+  if (height <= 0 || width <= 0 || height % 8 || width % 8)
+    return set_error(DCTF_EINVAL, "plane %dx%d: sides must be positive multiples of 8", height,
+                     width);
+  if (pitch < width || out_pitch < width || pitch % 4 || out_pitch % 4)
+    return set_error(DCTF_EINVAL, "pitches must be >= width and multiples of 4 floats");
+  if (!aligned16(coeffs) || !aligned16(out))
+    return set_error(DCTF_EINVAL, "planes must be 16-byte aligned");
+  const char *a = reinterpret_cast<const char *>(coeffs);
+  const char *b = reinterpret_cast<const char *>(out);
+  const size_t la = ((size_t)(height - 1) * pitch + width) * 4;
+  const size_t lb = ((size_t)(height - 1) * out_pitch + width) * 4;
+  if (a != b && a < b + lb && b < a + la)
+    return set_error(DCTF_EINVAL, "input and output planes overlap without being equal");
+  if (a == b && pitch != out_pitch)
+    return set_error(DCTF_EINVAL, "in place needs equal pitches");
+  cudaError_t e = launch_apply_planar(op, coeffs, height, width, pitch, out, out_pitch, op->d_err,
+                                      stream, (op->flags & DCTF_APPLY_INPUTS_READY) != 0);
+  if (e != cudaSuccess) return cuda_error(e, "dctf_apply_planar launch");
   return DCTF_OK;
 }
 

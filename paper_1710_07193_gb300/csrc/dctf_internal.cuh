@@ -69,6 +69,9 @@ struct dctf_operator {
   float *d_Gdc;             // n = 8: G[:, 0] in FP32
   __nv_bfloat16 *d_bf16;    // n = 16: BF16X6 pieces m0, m1, m2 (3 n2 rows per 64-chunk)
   uint32_t *d_tf32;         // n = 16: TF32 pieces hi, lo (2 n2 rows per 32-chunk)
+  bool kron;                // built with DCTF_BUILD_KRON: Kronecker factors kept
+  int krank;                //   number of terms of M = sum_t A_t kron B_t
+  float *d_kA, *d_kB;       //   [kMaxN][n][n] FP32 each (DCT-domain 1-D filters)
   uint32_t *d_err;          // device status word
   // dctf_apply_host staging (lazily allocated): kHostPipes streams, each
   // with an input and an output chunk buffer
@@ -97,6 +100,12 @@ inline bool tc_supported(int n, dctf_precision p) {
 }
 cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks,
                              float *y, cudaStream_t s);
+
+// kron.cu: the Kronecker (sandwich-product) form of the operator
+int kron_split_mask(const MaskParams &mp, double (*u)[kMaxN], double (*v)[kMaxN]);
+cudaError_t launch_kron_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s);
+cudaError_t launch_apply_kron(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
+                              cudaStream_t s);
 
 int sm_count(int device);
 

@@ -95,3 +95,52 @@ def test_mutant_is_caught(name, monkeypatch):
 def test_unmutated_oracle_passes_every_pin():
     for pin in _pins():
         pin()
+
+
+# ----------------------------------------------- Kronecker (sandwich) form
+from tests import test_oracle_kron as t_kron  # noqa: E402
+
+_orig_filter_1d = od.filter_1d
+_orig_kron_factors = od.kron_factors
+_orig_apply_kron = od.apply_kron
+
+
+def f1d_shifted_anchor(v, a, n, boundary):
+    return _orig_filter_1d(v, min(a + 1, len(v) - 1) if len(v) > 1 else a, n, boundary)
+
+
+def kf_swapped(w, anchor, n, boundary):
+    return [(b, a) for a, b in _orig_kron_factors(w, anchor, n, boundary)]
+
+
+def ak_untransposed(factors, coeffs, n):
+    return _orig_apply_kron([(a, b.T) for a, b in factors], coeffs, n)
+
+
+KRON_MUTANTS = {
+    "kron_anchor": ("filter_1d", f1d_shifted_anchor),
+    "kron_swapped": ("kron_factors", kf_swapped),
+    "kron_untransposed": ("apply_kron", ak_untransposed),
+}
+
+
+def _kron_pins():
+    return [
+        lambda: t_kron.test_kron_sum_equals_dense_operator(0, oracle.ZERO),
+        lambda: t_kron.test_kron_sum_equals_dense_operator(1, oracle.REPLICATE),
+        lambda: t_kron.test_sandwich_apply_equals_dense_apply(oracle.REPLICATE),
+    ]
+
+
+@pytest.mark.parametrize("name", sorted(KRON_MUTANTS))
+def test_kron_mutant_is_caught(name, monkeypatch):
+    attr, fn = KRON_MUTANTS[name]
+    monkeypatch.setattr(od, attr, fn)
+    monkeypatch.setattr(oracle, attr, fn)
+    failures = 0
+    for pin in _kron_pins():
+        try:
+            pin()
+        except AssertionError:
+            failures += 1
+    assert failures > 0, f"mutant {name} passed every pin"
