@@ -212,6 +212,18 @@ struct TileWalk {
   }
 };
 
+// uint8 of a filtered pixel: round half away from zero and saturate to
+// [0, 255] (Sec. III's conversion), on the FMA/ALU pipes only: clamp, add
+// 0.5, then add 2^23 rounding toward zero, which leaves floor(p + 0.5) in
+// the low mantissa bits.  (Rounding and float-to-integer conversion
+// instructions run on the slower XU pipe, which made the pixel epilogue
+// the bottleneck of the fused kernel.)  A value within one FP32 ulp below
+// a .5 boundary may round up: inside the 1e-4 tie band.
+__device__ __forceinline__ uint32_t pixel_u8(float p) {
+  const float c = fminf(fmaxf(p, 0.f), 255.f) + 0.5f;
+  return __float_as_uint(__fadd_rz(c, 8388608.0f)) & 0xffu;
+}
+
 // FP32 I/O: at most 152 registers a thread (58,368 of the SM's 65,536 for 384
 // threads), so the small FP64 operator-build kernels of the next image can
 // run on the same SMs while this kernel streams.
@@ -369,12 +381,16 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       float v[64];
       const uint8_t *st = s_in + s * L::kStageBytes + row * 128;
       if constexpr (kMode == kModePlanar) {
-        // shared [u][t.rows][v]: this block's row u is 32 bytes at (u t.rows + row) * 32
+        // shared [u][t.rows][v]: this block's row u is 32 bytes at (u t.rows + row) * 32.
+        // Lanes 4 apart hit the same banks; taking the two 16-byte halves in
+        // an order that flips with bit 2 of the row halves the conflicts.
         const uint8_t *sp = s_in + s * L::kStageBytes;
+        const int sw = (row >> 2) & 1;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const float4 *q = reinterpret_cast<const float4 *>(sp + (u * t.rows + row) * 32);
-          const float4 a = q[0], b = q[1];
+          const float4 f = q[sw], g = q[sw ^ 1];
+          const float4 a = sw ? g : f, b = sw ? f : g;
           v[8 * u] = a.x; v[8 * u + 1] = a.y; v[8 * u + 2] = a.z; v[8 * u + 3] = a.w;
           v[8 * u + 4] = b.x; v[8 * u + 5] = b.y; v[8 * u + 6] = b.z; v[8 * u + 7] = b.w;
         }
@@ -494,13 +510,10 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
             uint32_t w[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              uint32_t v = 0;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float p = fminf(fmaxf(roundf(acc[8 * i + 4 * h + e]), 0.f), 255.f);
-                v |= (uint32_t)p << (8 * e);
-              }
-              w[h] = v;
+              const float *a = acc + 8 * i + 4 * h;
+              // bytes b0..b3 into one word (PRMT: low bytes of four words)
+              w[h] = __byte_perm(__byte_perm(pixel_u8(a[0]), pixel_u8(a[1]), 0x0040),
+                                 __byte_perm(pixel_u8(a[2]), pixel_u8(a[3]), 0x0040), 0x5410);
             }
             *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
           }
@@ -514,12 +527,17 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       __syncwarp();
       uint8_t *slab = s_out + o * L::kStageBytes + wr * L::kSlabBytes;
       if constexpr (kMode == kModePlanar) {
-        // shared [u][32][v] for this warp's 32 blocks
+        // shared [u][32][v] for this warp's 32 blocks (halves in the
+        // converter's bank-friendly order)
+        const int sw = (r32 >> 2) & 1;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           float4 *q = reinterpret_cast<float4 *>(slab + (u * 32 + r32) * 32);
-          q[0] = make_float4(acc[8 * u], acc[8 * u + 1], acc[8 * u + 2], acc[8 * u + 3]);
-          q[1] = make_float4(acc[8 * u + 4], acc[8 * u + 5], acc[8 * u + 6], acc[8 * u + 7]);
+          const float4 a = make_float4(acc[8 * u], acc[8 * u + 1], acc[8 * u + 2], acc[8 * u + 3]);
+          const float4 b =
+              make_float4(acc[8 * u + 4], acc[8 * u + 5], acc[8 * u + 6], acc[8 * u + 7]);
+          q[sw] = sw ? b : a;
+          q[sw ^ 1] = sw ? a : b;
         }
       } else if constexpr (Io<IoT>::kBoxesPerRow == 2) {
 #pragma unroll
