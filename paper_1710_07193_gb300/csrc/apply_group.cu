@@ -79,15 +79,17 @@ template <> struct Io<int16_t> {
 constexpr int kBufs = 4;        // TMEM ring: [A_hi 32 | A_lo 32 | D 64] columns each
 constexpr int kDcRing = 2 * kBufs;
 
-// S input stages, NS operator slots (1 for a single item, 2 for groups)
-template <typename IoT, int S, int NS> struct Layout {
+// S input stages, NS operator slots (1 for a single item, 2 for groups), OB
+// output staging buffers (2; 0 for the pixel output, which stores from
+// registers and spends that shared memory on input stages instead)
+template <typename IoT, int S, int NS, int OB = 2> struct Layout {
   static constexpr int kStageBytes = kTile * Io<IoT>::kRowBytes;
   static constexpr int kBoxBytes = kTile * 128;              // one 128-row box
   static constexpr int kSlabBytes = 32 * Io<IoT>::kRowBytes; // one warp's output rows
   static constexpr int kSlabBoxBytes = 32 * 128;
   static constexpr int kOffIn = 0;
   static constexpr int kOffOut = kOffIn + S * kStageBytes;
-  static constexpr int kOffSlot = kOffOut + 2 * kStageBytes;
+  static constexpr int kOffSlot = kOffOut + OB * kStageBytes;
   static constexpr int kOffDc = kOffSlot + NS * kSlotBytes;
   static constexpr int kOffBar = kOffDc + kDcRing * kTile * 4;
   static constexpr int kNumBars = 2 * S + 3 * kBufs + kDcRing + 2 * NS;
@@ -234,7 +236,7 @@ __global__ void __maxnreg__(sizeof(IoT) == 4 ? 152 : 168)
 apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__ GroupItem single,
                    int nitems, int64_t total_halves, int max_take, int interleaved,
                    uint32_t *__restrict__ err) {
-  using L = Layout<IoT, S, NS>;
+  using L = Layout<IoT, S, NS, kMode == kModePixels ? 0 : 2>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -480,10 +482,13 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
           acc[32 + c] = __uint_as_float(d1[c]);
         }
       }
-      tc_fence_before();
-      mbar_arrive(&d_empty[b]);                      // D[b] may be overwritten now
+      // the DC value is read before D[b] is released: the converter rewrites
+      // this ring slot for tile it + 8 only after the MMAs of tile it + 4,
+      // which wait for that release
       if (!warp_wait_bounded(&dc_full[r], pr, s_abort, err, kRoleEpi | (it << 8))) break;
       const float x0 = s_dc[r * kTile + row];
+      tc_fence_before();
+      mbar_arrive(&d_empty[b]);                      // D[b] may be overwritten now
       const GroupItem &gi = items[t.item];
       const float out_scale = gi.out_scale;
       const uint8_t *slot = s_slot + k * kSlotBytes;
@@ -637,7 +642,7 @@ cudaError_t launch_cfg(const GroupItem *d_items, const GroupItem &single, int ni
                        int64_t total_halves, int grid, int max_take, int interleaved,
                        uint32_t *err, cudaStream_t s, bool pdl) {
   auto kern = apply_group_kernel<IoT, S, NS, kGroup, kMode>;
-  constexpr int smem = Layout<IoT, S, NS>::kSmem;
+  constexpr int smem = Layout<IoT, S, NS, kMode == kModePixels ? 0 : 2>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -683,6 +688,7 @@ cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, i
   int64_t g = grid > 0 ? grid : 0;
   if (g > total_halves) g = total_halves;
   if (g < 1) g = 1;
+  // four input stages, as for coefficients (six measured slower: 23.6 us)
   return launch_cfg<float, 4, 1, false, kModePixels>(nullptr, single, 1, total_halves, (int)g, 2,
                                                      1, err, s, pdl);
 }
