@@ -45,7 +45,7 @@ ROTATE = 8
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "38f005fbda8bc8ffb3e395624837ef54f1256b5d": 132032512,
+    "b17f90cac127bf30e98989d2370102d1d01b01df": 131896422,
 }
 
 

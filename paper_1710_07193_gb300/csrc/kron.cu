@@ -20,10 +20,11 @@
 // rank); one CTA per (term, side) forms the 1-D filter matrix and its DCT
 // form C H C^T in FP64 and stores it in FP32.
 //
-// Apply: 256 threads, thread = (block, row i).  Per term: U = X B_t^T row by
-// row (X row i in registers, B_t from shared memory by broadcast), U to
-// shared memory, then Y[i, :] += sum_k A_t[i, k] U[k, :] (a block's rows sit
-// in one warp, so warp-level synchronisation is enough).  FP32 throughout;
+// Apply: 256 threads, thread = (block, rows i and i + N/2).  Per term:
+// U = X B_t^T row by row (the two X rows in registers, B_t from shared
+// memory by broadcast), U to shared memory, then Y[r, :] += sum_k A_t[r, k]
+// U[k, :] (a block's threads sit in one warp, so warp-level
+// synchronisation is enough).  FP32 throughout;
 // as in the dense kernels the input DC coefficient (~N x the block mean) is
 // kept out of the products and added last as M[:,0] x[0], which keeps the
 // FP32 error near 1e-4 (without it, 1.2e-3 on the 4096^2 workload's mask).
@@ -83,12 +84,15 @@ __global__ void kron_build_kernel(const KronParams kp, const double *__restrict_
 
 constexpr int kThreads = 256;
 
+// Thread = (block, row pair i, i + N/2): every shared-memory load of B_t or
+// of a U row feeds two rows' multiply-adds.
 template <int N>
 __global__ void __launch_bounds__(kThreads, 2)
 apply_kron_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t nblocks,
                   const float *__restrict__ A, const float *__restrict__ B,
                   const float *__restrict__ Mdc, int rank) {
-  constexpr int BPC = kThreads / N;       // blocks per pass
+  constexpr int H = N / 2;                // threads per block
+  constexpr int BPC = kThreads / H;       // blocks per pass
   constexpr int LD = N + 4;               // padded row (16-byte aligned, fewer bank conflicts)
   extern __shared__ __align__(16) float smem_f[];
   float *sA = smem_f;                     // [rank][N][LD]
@@ -102,78 +106,94 @@ apply_kron_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t nb
   }
   for (int e = threadIdx.x; e < N * N; e += kThreads) sDc[e] = Mdc[e];
   __syncthreads();
-  const int lb = threadIdx.x / N, i = threadIdx.x % N;
+  const int lb = threadIdx.x / H, i = threadIdx.x % H;   // rows i and i + H
   float *u_blk = sU + lb * N * LD;
   for (int64_t b0 = (int64_t)blockIdx.x * BPC; b0 < nblocks; b0 += (int64_t)gridDim.x * BPC) {
     const int64_t b = b0 + lb;
-    const bool live = b < nblocks;        // warp-uniform per block (a block's rows share a warp)
-    float xr[N], yr[N];
+    const bool live = b < nblocks;
+    float x0r[N], x1r[N], y0r[N], y1r[N];
     if (live) {
-      const float4 *src = reinterpret_cast<const float4 *>(x + b * N * N + i * N);
+      const float4 *s0 = reinterpret_cast<const float4 *>(x + b * N * N + i * N);
+      const float4 *s1 = reinterpret_cast<const float4 *>(x + b * N * N + (i + H) * N);
 #pragma unroll
       for (int q = 0; q < N / 4; ++q) {
-        const float4 v = __ldcs(src + q);
-        xr[4 * q] = v.x; xr[4 * q + 1] = v.y; xr[4 * q + 2] = v.z; xr[4 * q + 3] = v.w;
+        const float4 v = __ldcs(s0 + q), w = __ldcs(s1 + q);
+        x0r[4 * q] = v.x; x0r[4 * q + 1] = v.y; x0r[4 * q + 2] = v.z; x0r[4 * q + 3] = v.w;
+        x1r[4 * q] = w.x; x1r[4 * q + 1] = w.y; x1r[4 * q + 2] = w.z; x1r[4 * q + 3] = w.w;
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < N; ++k) xr[k] = 0.f;
+      for (int k = 0; k < N; ++k) { x0r[k] = 0.f; x1r[k] = 0.f; }
     }
     // the block's DC coefficient, from its row-0 thread (first lane of the block)
-    const float x0 = __shfl_sync(0xffffffffu, xr[0], (threadIdx.x & 31) & ~(N - 1));
-    if (i == 0) xr[0] = 0.f;
+    const float xdc = __shfl_sync(0xffffffffu, x0r[0], (threadIdx.x & 31) & ~(H - 1));
+    if (i == 0) x0r[0] = 0.f;
 #pragma unroll
-    for (int k = 0; k < N; ++k) yr[k] = 0.f;
+    for (int k = 0; k < N; ++k) { y0r[k] = 0.f; y1r[k] = 0.f; }
     for (int t = 0; t < rank; ++t) {
-      // U[i][j] = sum_k X[i][k] B_t[j][k]
+      // U[r][j] = sum_k X[r][k] B_t[j][k] for r = i, i + H
       const float *bt = sB + t * N * N;
-      float ur[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        float acc = 0.f;
+      for (int jq = 0; jq < N / 4; ++jq) {
+        float u0[4], u1[4];
 #pragma unroll
-        for (int q = 0; q < N / 4; ++q) {
-          const float4 bv = *reinterpret_cast<const float4 *>(bt + j * N + 4 * q);
-          acc = fmaf(xr[4 * q], bv.x, acc);
-          acc = fmaf(xr[4 * q + 1], bv.y, acc);
-          acc = fmaf(xr[4 * q + 2], bv.z, acc);
-          acc = fmaf(xr[4 * q + 3], bv.w, acc);
+        for (int e = 0; e < 4; ++e) {
+          const int j = 4 * jq + e;
+          float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+          for (int q = 0; q < N / 4; ++q) {
+            const float4 bv = *reinterpret_cast<const float4 *>(bt + j * N + 4 * q);
+            a0 = fmaf(x0r[4 * q], bv.x, a0); a1 = fmaf(x1r[4 * q], bv.x, a1);
+            a0 = fmaf(x0r[4 * q + 1], bv.y, a0); a1 = fmaf(x1r[4 * q + 1], bv.y, a1);
+            a0 = fmaf(x0r[4 * q + 2], bv.z, a0); a1 = fmaf(x1r[4 * q + 2], bv.z, a1);
+            a0 = fmaf(x0r[4 * q + 3], bv.w, a0); a1 = fmaf(x1r[4 * q + 3], bv.w, a1);
+          }
+          u0[e] = a0; u1[e] = a1;
         }
-        ur[j] = acc;
+        *reinterpret_cast<float4 *>(u_blk + i * LD + 4 * jq) = make_float4(u0[0], u0[1], u0[2], u0[3]);
+        *reinterpret_cast<float4 *>(u_blk + (i + H) * LD + 4 * jq) =
+            make_float4(u1[0], u1[1], u1[2], u1[3]);
       }
-#pragma unroll
-      for (int q = 0; q < N / 4; ++q)
-        *reinterpret_cast<float4 *>(u_blk + i * LD + 4 * q) =
-            make_float4(ur[4 * q], ur[4 * q + 1], ur[4 * q + 2], ur[4 * q + 3]);
       __syncwarp();
-      // Y[i][:] += sum_k A_t[i][k] U[k][:]
-      const float *at = sA + (t * N + i) * LD;
+      // Y[r][:] += sum_k A_t[r][k] U[k][:]
+      const float *at0 = sA + (t * N + i) * LD, *at1 = sA + (t * N + i + H) * LD;
 #pragma unroll
       for (int kq = 0; kq < N / 4; ++kq) {
-        const float4 a4 = *reinterpret_cast<const float4 *>(at + 4 * kq);
-        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float4 p4 = *reinterpret_cast<const float4 *>(at0 + 4 * kq);
+        const float4 q4 = *reinterpret_cast<const float4 *>(at1 + 4 * kq);
+        const float av0[4] = {p4.x, p4.y, p4.z, p4.w}, av1[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int k = 4 * kq + e;
 #pragma unroll
           for (int q = 0; q < N / 4; ++q) {
             const float4 uv = *reinterpret_cast<const float4 *>(u_blk + k * LD + 4 * q);
-            yr[4 * q] = fmaf(av[e], uv.x, yr[4 * q]);
-            yr[4 * q + 1] = fmaf(av[e], uv.y, yr[4 * q + 1]);
-            yr[4 * q + 2] = fmaf(av[e], uv.z, yr[4 * q + 2]);
-            yr[4 * q + 3] = fmaf(av[e], uv.w, yr[4 * q + 3]);
+            y0r[4 * q] = fmaf(av0[e], uv.x, y0r[4 * q]);
+            y0r[4 * q + 1] = fmaf(av0[e], uv.y, y0r[4 * q + 1]);
+            y0r[4 * q + 2] = fmaf(av0[e], uv.z, y0r[4 * q + 2]);
+            y0r[4 * q + 3] = fmaf(av0[e], uv.w, y0r[4 * q + 3]);
+            y1r[4 * q] = fmaf(av1[e], uv.x, y1r[4 * q]);
+            y1r[4 * q + 1] = fmaf(av1[e], uv.y, y1r[4 * q + 1]);
+            y1r[4 * q + 2] = fmaf(av1[e], uv.z, y1r[4 * q + 2]);
+            y1r[4 * q + 3] = fmaf(av1[e], uv.w, y1r[4 * q + 3]);
           }
         }
       }
       __syncwarp();                       // U is rewritten by the next term
     }
 #pragma unroll
-    for (int k = 0; k < N; ++k) yr[k] = fmaf(sDc[i * N + k], x0, yr[k]);
+    for (int k = 0; k < N; ++k) {
+      y0r[k] = fmaf(sDc[i * N + k], xdc, y0r[k]);
+      y1r[k] = fmaf(sDc[(i + H) * N + k], xdc, y1r[k]);
+    }
     if (live) {
-      float4 *dst = reinterpret_cast<float4 *>(y + b * N * N + i * N);
+      float4 *d0 = reinterpret_cast<float4 *>(y + b * N * N + i * N);
+      float4 *d1 = reinterpret_cast<float4 *>(y + b * N * N + (i + H) * N);
 #pragma unroll
-      for (int q = 0; q < N / 4; ++q)
-        __stcs(dst + q, make_float4(yr[4 * q], yr[4 * q + 1], yr[4 * q + 2], yr[4 * q + 3]));
+      for (int q = 0; q < N / 4; ++q) {
+        __stcs(d0 + q, make_float4(y0r[4 * q], y0r[4 * q + 1], y0r[4 * q + 2], y0r[4 * q + 3]));
+        __stcs(d1 + q, make_float4(y1r[4 * q], y1r[4 * q + 1], y1r[4 * q + 2], y1r[4 * q + 3]));
+      }
     }
   }
 }
@@ -181,7 +201,7 @@ apply_kron_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t nb
 template <int N>
 cudaError_t launch_apply(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
                          cudaStream_t s) {
-  constexpr int BPC = kThreads / N, LD = N + 4;
+  constexpr int BPC = kThreads / (N / 2), LD = N + 4;
   const int smem =
       (op->krank * N * LD + op->krank * N * N + BPC * N * LD + N * N) * (int)sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(apply_kron_kernel<N>,
