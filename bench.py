@@ -259,10 +259,14 @@ def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
                         "max_batch": st["max_batch_requests_seen"],
                         "cache_hit_rate": st["cache_hits"] / max(1, st["cache_hits"] + st["cache_misses"]),
                         "failed": st["failed"]})
-    ok = [r for r in results if r["p99_ms"] < 10.0]
+    # the headline rate must also be sustained: the stream finished at >= 90%
+    # of the offered rate (the single-threaded Python submitter tops out
+    # between 6k and 8k requests/s)
+    ok = [r for r in results if r["p99_ms"] < 10.0 and r["requests_per_s"] >= 0.9 * r["rate_req_s"]]
     return {"stream": "Poisson; 50% 1920x1088 4:2:0 frames, 50% 512x512 stills; int16, "
                       "q[u,v]=1+round(s(1+u+v)), s in {1,2,4}; 32 seeded masks 3x3..7x7; "
                       "page-locked host buffers",
+            "headline_rule": "highest offered rate with p99 < 10 ms and >= 90% of it sustained",
             "rates": results,
             "headline": max(ok, key=lambda r: r["rate_req_s"]) if ok else None}
 

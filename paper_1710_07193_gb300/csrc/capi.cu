@@ -321,6 +321,7 @@ dctf_status dctf_apply_pixels(const dctf_operator *op, const float *coeffs, int 
   if (!aligned16(coeffs) || (reinterpret_cast<uintptr_t>(image) & 7))
     return set_error(DCTF_EINVAL, "coeffs must be 16-byte and image 8-byte aligned");
   const int64_t nblocks = (int64_t)(height / 8) * (width / 8);
+  if (nblocks > ((int64_t)1 << 31) - 128) return set_error(DCTF_EINVAL, "image too large");
   const char *a = reinterpret_cast<const char *>(coeffs);
   const char *b = reinterpret_cast<const char *>(image);
   const size_t la = (size_t)nblocks * 64 * sizeof(float), lb = (size_t)(height - 1) * pitch + width;
@@ -355,6 +356,9 @@ dctf_status dctf_apply_planar(const dctf_operator *op, const float *coeffs, int 
     return set_error(DCTF_EINVAL, "pitches must be >= width and multiples of 4 floats");
   if (!aligned16(coeffs) || !aligned16(out))
     return set_error(DCTF_EINVAL, "planes must be 16-byte aligned");
+  // the tile walk runs over block rows padded to 128 blocks, in 32-bit indices
+  if ((int64_t)(height / 8) * ((width / 8 + 127) / 128 * 128) > ((int64_t)1 << 31) - 128)
+    return set_error(DCTF_EINVAL, "plane too large");
   const char *a = reinterpret_cast<const char *>(coeffs);
   const char *b = reinterpret_cast<const char *>(out);
   const size_t la = ((size_t)(height - 1) * pitch + width) * 4;
