@@ -157,6 +157,25 @@ def cpu_oracle_sample(job, x, n_sample: int, reps_target_s: float):
     return reps * n_sample / dt, reps, dt
 
 
+def oracle_parity(job, x_sample, y_gpu):
+    """Parity of the timed kernel's output with the FP64 oracle on the CPU
+    baseline's sample: coefficient error, and uint8 pixels against the
+    oracle's spatial-domain filter outside the 1e-4 tie band."""
+    import oracle
+    n = x_sample.shape[0]
+    y_ref = oracle.apply_M(oracle.build_M(job.mask, job.anchor, 8, job.boundary),
+                           x_sample.astype(np.float64))
+    err = np.abs(y_gpu.astype(np.float64) - y_ref)
+    blocks = oracle.image_to_blocks(job.image, 8)[:n]
+    p_sp = oracle.spatial_filter_blocks(blocks, job.mask, job.anchor, job.boundary)
+    st = oracle.uint8_compare(p_sp, oracle.to_uint8(oracle.idct2_blocks(y_gpu.astype(np.float64), 8)),
+                              1e-4)
+    return {"blocks": n, "max_coef_err": float(err.max()),
+            "max_coef_err_rel": float(err.max() / np.abs(y_ref).max()),
+            "uint8_mismatch": int(st["mismatch"]), "uint8_tie_band": int(st["band"]),
+            "pixels": int(st["total"]), "bar": "coefficients <= 1e-3; uint8 equal outside the band"}
+
+
 def oracle_coefficients(job):
     import oracle
     return oracle.dct2_blocks(oracle.image_to_blocks(job.image, 8)).astype(np.float32)
@@ -595,7 +614,7 @@ def run_dctf(args):
     e_dt = time.perf_counter() - e0
     e2e = {"value": ws * nb * e2e_steps / e_dt, "unit": UNIT,
            "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
-           "steps": e2e_steps, "path": "dctf_apply_host, pinned host buffers, 4 MB chunks on 4 streams"}
+           "steps": e2e_steps, "path": "dctf_apply_host, pinned host buffers, 8 MB chunks on 4 streams"}
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -644,6 +663,13 @@ def run_dctf(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{reps} x (operator build + apply to 65536 of the "
                                           f"262144 blocks), {dt:.1f} s, numpy FP64"}
+        # the timed F16X3 kernel's output on the same sample, checked by the oracle
+        ops[0].set_precision(lib.F16X3)
+        ops[0].set_flags(0)
+        yp = torch.empty((65536, 64), dtype=torch.float32, device=dev)
+        lib.apply(ops[0], x0, 65536, yp)
+        torch.cuda.synchronize()
+        line["cpu_baseline"]["parity"] = oracle_parity(job, x_host[:65536], yp.cpu().numpy())
     if rank == 0:
         print(json.dumps(line), flush=True)
     for o in ops:

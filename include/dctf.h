@@ -217,13 +217,14 @@ dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs,
                              dctf_stream_t stream);
 
 /* End-to-end call for callers holding the data in HOST memory: copies
- * host_in to the device, applies, copies the result to host_out, in 4 MB
+ * host_in to the device, applies, copies the result to host_out, in 8 MB
  * chunks pipelined over four internal streams and device buffers owned by
  * the operator.  The internal streams are blocking streams: the copies start
  * after work already queued on the legacy default stream (e.g. a rebuild).
  * Synchronous: returns after host_out is written.  host_in and host_out
  * should be pinned (cudaHostAlloc) for full speed.  The first call allocates
- * the staging buffers (8 x 4 MB). */
+ * the staging buffers (8 x 8 MB).  Never uses programmatic dependent launch
+ * (each apply follows the copy of its input). */
 dctf_status dctf_apply_host(dctf_operator *op, const float *host_in,
                             int64_t nblocks, float *host_out);
 

@@ -79,6 +79,7 @@ struct dctf_operator {
   float *d_stage[kHostPipes][2];
   size_t stage_blocks;
   cudaStream_t host_streams[kHostPipes];
+  void *h_pipe_items;       // 8x8 F16X3: each pipe's full-chunk work item, encoded once
 };
 
 namespace dctf {

@@ -215,6 +215,22 @@ def test_apply_host_matches_device(dctf, ragged_source):
     hout = torch.empty_like(hin).pin_memory()
     dctf.apply_host(op, hin, x.shape[0], hout)
     assert np.array_equal(hout.numpy().astype(np.float64), y_dev)
+    # more blocks than one 8 MB chunk (full chunks take the pre-encoded
+    # pipe items, the tail the general path), after a rebuild that changes
+    # the operator's scale, and with the inputs-ready flag set (which the
+    # host path must not apply: each apply follows its input copy)
+    xx = np.concatenate([x] * 3)
+    w2 = datagen.magic_square_3()
+    op.rebuild(w2, (1, 1), dctf.REPLICATE)
+    op.set_flags(dctf.APPLY_INPUTS_READY)
+    y2 = run(dctf, op, xx, dctf.F16X3)
+    hin2 = torch.from_numpy(xx).pin_memory()
+    hout2 = torch.empty_like(hin2).pin_memory()
+    for _ in range(2):
+        hout2.zero_()
+        dctf.apply_host(op, hin2, xx.shape[0], hout2)
+        assert np.array_equal(hout2.numpy().astype(np.float64), y2)
+    op.release()
 
 
 @pytest.fixture(scope="module")
