@@ -224,7 +224,8 @@ dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs,
  * Synchronous: returns after host_out is written.  host_in and host_out
  * should be pinned (cudaHostAlloc) for full speed.  The first call allocates
  * the staging buffers (8 x 8 MB).  Never uses programmatic dependent launch
- * (each apply follows the copy of its input). */
+ * (each apply follows the copy of its input).  Calls on the same operator
+ * from several host threads are serialised (the staging is per operator). */
 dctf_status dctf_apply_host(dctf_operator *op, const float *host_in,
                             int64_t nblocks, float *host_out);
 

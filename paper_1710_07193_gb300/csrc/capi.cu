@@ -397,6 +397,7 @@ dctf_status dctf_apply_host(dctf_operator *op, const float *host_in, int64_t nbl
   if (nblocks < 0) return set_error(DCTF_EINVAL, "nblocks < 0");
   if (nblocks == 0) return DCTF_OK;
   if (host_in == nullptr || host_out == nullptr) return set_error(DCTF_EINVAL, "NULL buffer");
+  std::lock_guard<std::mutex> lock(op->host_mu);   // the staging buffers are per operator
   constexpr int P = dctf_operator::kHostPipes;
   const size_t row = (size_t)op->n2 * sizeof(float);
   const int64_t chunk = (int64_t)((8u << 20) / row);    // 8 MB of coefficients per chunk (4 MB measured slower)

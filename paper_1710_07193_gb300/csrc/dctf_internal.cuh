@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "dctf.h"
@@ -80,6 +81,7 @@ struct dctf_operator {
   size_t stage_blocks;
   cudaStream_t host_streams[kHostPipes];
   void *h_pipe_items;       // 8x8 F16X3: each pipe's full-chunk work item, encoded once
+  std::mutex host_mu;       // serialises dctf_apply_host calls on this operator
 };
 
 namespace dctf {
