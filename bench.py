@@ -45,7 +45,7 @@ ROTATE = 8
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "b17f90cac127bf30e98989d2370102d1d01b01df": 131896422,
+    "7dd4beac2c4c6c595a805576d682d8aa831e6e7d": 131932313,
 }
 
 
@@ -612,9 +612,14 @@ def run_dctf(args):
         op.rebuild(job.mask, job.anchor, job.boundary)
         lib.apply_host(op, hin, nb, hout)
     e_dt = time.perf_counter() - e0
+    direct = (lib.host_buffer_direct(hin, hin.numel() * 4)
+              and lib.host_buffer_direct(hout, hout.numel() * 4))
+    route = ("host-direct route: one launch whose 32 CTAs read the input from and write the "
+             "output to the page-locked host buffers over the host link (no device staging)"
+             if direct else "staged route: 8 MB chunks, copy in / apply / copy out on 4 streams")
     e2e = {"value": ws * nb * e2e_steps / e_dt, "unit": UNIT,
            "h2d_bytes_per_step": int(hin.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
-           "steps": e2e_steps, "path": "dctf_apply_host, pinned host buffers, 8 MB chunks on 4 streams"}
+           "steps": e2e_steps, "path": "dctf_apply_host (operator rebuild + apply per step), " + route}
 
     serving = None
     if rank == 0 and not args.no_serving:

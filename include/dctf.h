@@ -216,18 +216,32 @@ dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs,
                              int64_t nblocks, float *out,
                              dctf_stream_t stream);
 
-/* End-to-end call for callers holding the data in HOST memory: copies
- * host_in to the device, applies, copies the result to host_out, in 8 MB
- * chunks pipelined over four internal streams and device buffers owned by
- * the operator.  The internal streams are blocking streams: the copies start
- * after work already queued on the legacy default stream (e.g. a rebuild).
- * Synchronous: returns after host_out is written.  host_in and host_out
- * should be pinned (cudaHostAlloc) for full speed.  The first call allocates
- * the staging buffers (8 x 8 MB).  Never uses programmatic dependent launch
- * (each apply follows the copy of its input).  Calls on the same operator
- * from several host threads are serialised (the staging is per operator). */
+/* End-to-end call for callers holding the data in HOST memory (the same
+ * y_b = M x_b as dctf_apply).  host_in, host_out: [nblocks][N*N] FP32 in
+ * host memory, owned by the caller; host_out == host_in allowed, no other
+ * overlap (EINVAL).  Two routes, chosen per call:
+ *  - 8x8 DCTF_F16X3 with both buffers page-locked and mapped (cudaHostAlloc,
+ *    cudaHostRegister; see dctf_host_buffer_direct) and 16-byte aligned: ONE
+ *    host-direct launch of the tensor-core kernel, which reads host_in and
+ *    writes host_out over the host link itself (no device staging), with the
+ *    same arithmetic and result as dctf_apply;
+ *  - otherwise host_in is copied to the device, applied and copied back in
+ *    8 MB chunks pipelined over four internal streams and device buffers
+ *    owned by the operator (allocated by the first such call, 8 x 8 MB).
+ * The internal streams are blocking streams: the work starts after work
+ * already queued on the legacy default stream (e.g. a rebuild).
+ * Synchronous: returns after host_out is written.  Never uses programmatic
+ * dependent launch.  Calls on the same operator from several host threads
+ * are serialised (the streams and staging are per operator). */
 dctf_status dctf_apply_host(dctf_operator *op, const float *host_in,
                             int64_t nblocks, float *host_out);
+
+/* 1 if [p, p + bytes) is host memory that kernels can read and write
+ * directly: page-locked, mapped into the device address space, inside one
+ * allocation (dctf_apply_host then takes its host-direct route); 0
+ * otherwise (pageable memory, device memory, NULL, bytes < 0).  Host-side
+ * query, no device work. */
+int dctf_host_buffer_direct(const void *p, int64_t bytes);
 
 /* ---------------------------------------------------------------------
  * Grouped apply: many images, each with its own operator, in ONE persistent

@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3", "KRON_FP32",
     "DctfError", "load", "lib_path", "exported_symbols", "build_operator", "Operator",
-    "apply", "apply_f64in", "apply_host", "apply_pixels", "apply_planar", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
+    "apply", "apply_f64in", "apply_host", "host_buffer_direct", "apply_pixels", "apply_planar", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
     "version", "IO_F32", "IO_I16", "Group", "group_create", "apply_grouped", "Server",
 ]
 
@@ -49,6 +49,7 @@ _SIGS = {
     "dctf_apply_pixels": (_i32, [_vp, _vp, _i32, _i32, _vp, _i64, _vp]),
     "dctf_apply_planar": (_i32, [_vp, _vp, _i32, _i32, _i64, _vp, _i64, _vp]),
     "dctf_apply_host": (_i32, [_vp, _vp, _i64, _vp]),
+    "dctf_host_buffer_direct": (_i32, [_vp, _i64]),
     "dctf_forward_dct": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
     "dctf_forward_dct_f64": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp]),
     "dctf_forward_dct_i16": (_i32, [_vp, _i32, _i32, _i64, _i32, _vp, _vp, _vp]),
@@ -249,8 +250,15 @@ def selftest_wait_timeout(limit_us: int = 2000) -> tuple[int, int, int]:
 
 
 def apply_host(op: Operator, host_in, nblocks: int, host_out) -> None:
-    """Host buffers in and out; copies and compute pipelined inside the library."""
+    """Host buffers in and out: one host-direct launch on page-locked mapped
+    buffers (8x8 F16X3), else copies and compute pipelined in the library."""
     _check(load().dctf_apply_host(op.handle, _ptr(host_in), nblocks, _ptr(host_out)))
+
+
+def host_buffer_direct(buf, nbytes: int) -> bool:
+    """True if the device can read and write `buf` (nbytes from its start)
+    directly: page-locked, mapped, inside one allocation."""
+    return load().dctf_host_buffer_direct(_ptr(buf), nbytes) == 1
 
 
 class _GroupItem(ctypes.Structure):

@@ -2,7 +2,7 @@
 
 Translation units compile in parallel into ``_build/`` at the repository root;
 the shared library lands next to this file.  The CUDA runtime is linked
-statically and libcuda is not linked (its one driver entry point is fetched at
+statically and libcuda is not linked (its driver entry points are fetched at
 run time), so the library loads on a machine without a GPU.
 """
 from __future__ import annotations

@@ -41,6 +41,13 @@
 //    box and stores 32 blocks per epilogue warp the same way; block rows
 //    are padded to a multiple of 128 blocks in the tile walk (the padding
 //    is outside the tensor: zero-filled on load, clipped on store).
+//  * Host-direct I/O (kMode = kModeHost): the coefficients stay in page-locked
+//    host memory mapped into the device address space.  The whole producer
+//    warp copies each 32 KB input tile with 16-byte cp.async into the same
+//    swizzled stage layout the TMA box gives (zero-filled past the last
+//    block), and the epilogue warps write their staged outputs to host
+//    memory with coalesced 16-byte stores.  Every byte crosses the host link
+//    once each way, with no device buffer and no copy engine.
 //
 // Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM
 // allocator, warp 3 slot loader, warps 4-7 converter (thread = tile row),
@@ -229,7 +236,7 @@ __device__ __forceinline__ uint32_t pixel_u8(float p) {
 // FP32 I/O: at most 152 registers a thread (58,368 of the SM's 65,536 for 384
 // threads), so the small FP64 operator-build kernels of the next image can
 // run on the same SMs while this kernel streams.
-enum : int { kModeBlocks = 0, kModePixels = 1, kModePlanar = 2 };
+enum : int { kModeBlocks = 0, kModePixels = 1, kModePlanar = 2, kModeHost = 3 };
 
 template <typename IoT, int S, int NS, bool kGroup, int kMode>
 __global__ void __maxnreg__(sizeof(IoT) == 4 ? 152 : 168)
@@ -260,7 +267,11 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) { mbar_init(&full_in[s], 1); mbar_init(&empty_in[s], 128); }
+    // host-direct input: one cp.async arrival per producer lane
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_in[s], kMode == kModeHost ? 32 : 1);
+      mbar_init(&empty_in[s], 128);
+    }
     for (int b = 0; b < kBufs; ++b) {
       mbar_init(&a_full[b], 128); mbar_init(&mma_done[b], 1); mbar_init(&d_empty[b], 128);
     }
@@ -282,7 +293,38 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
   walk.init(items, nitems, total_halves, max_take, interleaved != 0);
   Tile t;
 
-  if (warp == 0 && lane == 0) {
+  if (kMode == kModeHost && warp == 0) {
+    // ---------------------------------------------------------- host producer
+    // The tile's rows are contiguous: chunk c (16 bytes) of the tile is
+    // coefficients 4 (c % 16) .. +3 of row c / 16, and lane l copies chunks
+    // l, l + 32, ...  (a warp reads 512 contiguous bytes per step).  Each
+    // chunk lands where the 128-byte-swizzled TMA box would put it.
+    int it = 0;
+    while (walk.next(t)) {
+      const int s = it % S;
+      const uint32_t ph = (it / S) & 1;
+      if (!warp_wait_bounded(&empty_in[s], ph ^ 1, s_abort, err, kRoleProducer | (it << 8))) break;
+      const GroupItem &gi = items[t.item];
+      const int64_t left = gi.nblocks - t.row0;
+      const int valid = left < t.rows ? (int)left : t.rows;     // rows past the end: zeros
+      const float4 *src = reinterpret_cast<const float4 *>(gi.hin) + (int64_t)t.row0 * 16;
+      const uint32_t dst = smem_u32(s_in + s * L::kStageBytes);
+      const int nchunks = t.rows * 16;
+#pragma unroll 8
+      for (int c = lane; c < nchunks; c += 32) {
+        const int r = c >> 4, u = c & 15;
+        const uint32_t d = dst + (u >> 3) * L::kBoxBytes + r * 128 + (((u & 7) ^ (r & 7)) << 4);
+        const bool ok = r < valid;
+        cp_async_16(d, ok ? src + c : src, ok ? 16u : 0u);
+      }
+      cp_async_arrive(&full_in[s]);
+      ++it;
+    }
+    cp_async_wait_all();
+    if (lane == 0)
+      for (int q = it > S ? it - S : 0; q < it; ++q)
+        wait_drain(&full_in[q % S], (q / S) & 1, err, kRoleDrain);
+  } else if (kMode != kModeHost && warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
     int it = 0, issued = 0;
     while (walk.next(t)) {
@@ -528,9 +570,36 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         continue;
       }
       const bool store = wr * 32 < t.rows;
+      uint8_t *slab = s_out + o * L::kStageBytes + wr * L::kSlabBytes;
+      if constexpr (kMode == kModeHost) {
+        // stage this warp's 32 rows (swizzled as for the TMA store), then
+        // copy them out: chunk c = lane + 32 i is 16 bytes of row c / 16, so
+        // a warp writes 512 contiguous bytes per step.  Slab o was last read
+        // two tiles ago, before the __syncwarp of the previous tile.
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          *reinterpret_cast<float4 *>(slab + (u >> 3) * L::kSlabBoxBytes + r32 * 128 +
+                                      (((u & 7) ^ (r32 & 7)) << 4)) =
+              make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
+        __syncwarp();
+        if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's M[:,0]
+        const int64_t y0 = (int64_t)t.row0 + wr * 32;
+        const int64_t left = gi.nblocks - y0;
+        const int lim = t.rows - wr * 32 < 32 ? t.rows - wr * 32 : 32;
+        const int nrows = (int)(left < lim ? left : lim);     // <= 0: nothing to store
+        float4 *dst = reinterpret_cast<float4 *>(gi.hout) + y0 * 16;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = lane + 32 * i, r = c >> 4, u = c & 15;
+          if (r < nrows)
+            __stcs(dst + c, *reinterpret_cast<const float4 *>(
+                                slab + (u >> 3) * L::kSlabBoxBytes + r * 128 + (((u & 7) ^ (r & 7)) << 4)));
+        }
+        ++it;
+        continue;
+      }
       if (lane == 0) bulk_wait_read<1>();             // slab o free (store of tile it-2 read it)
       __syncwarp();
-      uint8_t *slab = s_out + o * L::kStageBytes + wr * L::kSlabBytes;
       if constexpr (kMode == kModePlanar) {
         // shared [u][32][v] for this warp's 32 blocks (halves in the
         // converter's bank-friendly order)
@@ -730,6 +799,18 @@ cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int he
   if (g < 1) g = 1;
   return launch_cfg<float, 4, 1, false, kModePlanar>(nullptr, gi, 1, total_halves, (int)g, 2, 1,
                                                      err, s, pdl);
+}
+
+cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halves, int grid,
+                                     uint32_t *err, cudaStream_t s) {
+  if (total_halves <= 0) return cudaSuccess;
+  int64_t g = grid > 0 ? grid : 0;
+  if (g > total_halves) g = total_halves;
+  if (g < 1) g = 1;
+  // 64-block tiles dealt round-robin: the CTAs work on adjacent tiles, so the
+  // host memory in flight stays one compact window
+  return launch_cfg<float, 4, 1, false, kModeHost>(nullptr, single, 1, total_halves, (int)g, 1, 1,
+                                                   err, s, false);
 }
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,

@@ -28,6 +28,8 @@ struct GroupItem {              // CUtensorMap members keep it 128-byte aligned
   uint8_t *img;             // pixel output (apply_pixels): uint8 image,
   int64_t pitch;            //   its row pitch in bytes,
   int64_t bw;               //   and its width in blocks
+  const float *hin;         // host-direct apply: mapped page-locked host input
+  float *hout;              //   and output, [nblocks][64] FP32, 16-byte aligned
 };
 
 cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *in, void *out,
@@ -50,6 +52,16 @@ cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, i
 cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int height, int width,
                                 int64_t in_pitch, float *out, int64_t out_pitch, uint32_t *err,
                                 cudaStream_t s, bool pdl);
+
+// Host-direct apply, one item (8x8 blocks, F16X3, FP32 coefficients): the
+// producer warp copies each input tile from item.hin (page-locked host
+// memory, mapped) with 16-byte cp.async and the epilogue writes item.hout
+// with plain stores, so the coefficients cross the host link once each way
+// with no device staging.  Same arithmetic and per-block order as
+// launch_apply_group.  `grid` CTAs (the host link bounds this launch, not
+// the SMs), 64-block tiles.  Never uses programmatic dependent launch.
+cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halves, int grid,
+                                     uint32_t *err, cudaStream_t s);
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,

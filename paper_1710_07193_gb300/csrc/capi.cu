@@ -42,6 +42,52 @@ int sm_count(int device) {
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Host memory a kernel can read and write directly: page-locked
+// (cudaHostAlloc, cudaHostRegister), mapped into the device address space,
+// with [p, p + bytes) inside one allocation.  Returns the device address of
+// p, or nullptr (pageable memory, a range past the allocation, or a failed
+// query).
+typedef CUresult (*PointerAttrFn)(void *, CUpointer_attribute, CUdeviceptr);
+static PointerAttrFn pointer_attr_fn() {
+  static PointerAttrFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PointerAttrFn>(f);
+  });
+  return fn;
+}
+// CTAs of the host-direct launch.  The host link, not the SMs, bounds it
+// (~330 GB/s both directions together on GB300, by copy engine or by kernel
+// loads alike); measured on 262,144 blocks, 16-48 CTAs reach it (412-435 us)
+// while one CTA per SM (152) gives 525 us: fewer concurrent request streams
+// over a narrower window of host memory move faster.
+constexpr int kHostDirectCtas = 32;
+
+static void *mapped_host(const void *p, size_t bytes) {
+  if (p == nullptr) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+  PointerAttrFn f = pointer_attr_fn();
+  if (f == nullptr) return nullptr;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  const CUdeviceptr q = reinterpret_cast<CUdeviceptr>(p);
+  if (f(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, q) != CUDA_SUCCESS ||
+      f(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, q) != CUDA_SUCCESS)
+    return nullptr;
+  if (q < start || q - start > size || bytes > size - (q - start)) return nullptr;
+  return a.devicePointer;
+}
+
 static dctf_status check_mask(const double *mask, int mh, int mw, const int anchor[2],
                               int n, int boundary, MaskParams *mp) {
   if (n != 4 && n != 8 && n != 16)
@@ -391,21 +437,56 @@ dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs, int6
   return DCTF_OK;
 }
 
+int dctf_host_buffer_direct(const void *p, int64_t bytes) {
+  return bytes >= 0 && mapped_host(p, (size_t)bytes) != nullptr ? 1 : 0;
+}
+
 dctf_status dctf_apply_host(dctf_operator *op, const float *host_in, int64_t nblocks,
                             float *host_out) {
   if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
   if (nblocks < 0) return set_error(DCTF_EINVAL, "nblocks < 0");
   if (nblocks == 0) return DCTF_OK;
   if (host_in == nullptr || host_out == nullptr) return set_error(DCTF_EINVAL, "NULL buffer");
-  std::lock_guard<std::mutex> lock(op->host_mu);   // the staging buffers are per operator
-  constexpr int P = dctf_operator::kHostPipes;
+  if (nblocks > ((int64_t)1 << 31) - 128) return set_error(DCTF_EINVAL, "nblocks too large");
   const size_t row = (size_t)op->n2 * sizeof(float);
+  {
+    const char *a = reinterpret_cast<const char *>(host_in), *b = reinterpret_cast<char *>(host_out);
+    const size_t len = (size_t)nblocks * row;
+    if (a != b && a < b + len && b < a + len)
+      return set_error(DCTF_EINVAL, "input and output overlap without being equal");
+  }
+  std::lock_guard<std::mutex> lock(op->host_mu);   // the streams and staging are per operator
+  constexpr int P = dctf_operator::kHostPipes;
+  if (op->host_streams[0] == nullptr)
+    for (int i = 0; i < P; ++i)
+      DCTF_CUDA(cudaStreamCreateWithFlags(&op->host_streams[i], cudaStreamDefault));
+  // 8x8 F16X3 on page-locked mapped host memory: one host-direct launch
+  // reads the input and writes the output over the host link itself (no
+  // device staging, no copy-engine pipeline to fill and drain)
+  if (op->n == 8 && op->precision == DCTF_F16X3 && aligned16(host_in) && aligned16(host_out)) {
+    const void *din = mapped_host(host_in, (size_t)nblocks * row);
+    void *dout = din ? mapped_host(host_out, (size_t)nblocks * row) : nullptr;
+    if (dout != nullptr) {
+      GroupItem gi;
+      memset(&gi, 0, sizeof gi);
+      gi.pieces = op->d_f16;
+      gi.mdc = op->d_Mdc;
+      gi.out_scale = ldexpf(1.0f, -op->f16_scale_exp);
+      gi.nblocks = nblocks;
+      gi.hin = static_cast<const float *>(din);
+      gi.hout = static_cast<float *>(dout);
+      cudaStream_t s = op->host_streams[0];
+      cudaError_t e = launch_apply_host_direct(gi, (nblocks + 63) / 64, kHostDirectCtas,
+                                               op->d_err, s);
+      if (e != cudaSuccess) return cuda_error(e, "dctf_apply_host launch");
+      DCTF_CUDA(cudaStreamSynchronize(s));
+      return DCTF_OK;
+    }
+  }
   const int64_t chunk = (int64_t)((8u << 20) / row);    // 8 MB of coefficients per chunk (4 MB measured slower)
   if (op->d_stage[0][0] == nullptr) {
-    for (int i = 0; i < P; ++i) {
+    for (int i = 0; i < P; ++i)
       for (int j = 0; j < 2; ++j) DCTF_CUDA(cudaMalloc(&op->d_stage[i][j], chunk * row));
-      DCTF_CUDA(cudaStreamCreateWithFlags(&op->host_streams[i], cudaStreamDefault));
-    }
     op->stage_blocks = chunk;
   }
   // 8x8 F16X3: each pipe's work item (tensor maps of its fixed staging

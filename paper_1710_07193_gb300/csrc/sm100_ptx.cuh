@@ -154,6 +154,24 @@ template <int N>
 __device__ __forceinline__ void bulk_wait() {
   asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
 }
+// 16-byte non-bulk asynchronous copy global -> shared (cached in L2 only).
+// Copies src_bytes (0 or 16) and zero-fills the rest; with 0 nothing is
+// read.  Used where the source is page-locked host memory mapped into the
+// device address space.
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst),
+               "l"(static_cast<uint64_t>(__cvta_generic_to_global(src))), "r"(src_bytes)
+               : "memory");
+}
+// One arrival on `bar` once every cp.async this thread issued so far has
+// landed; the barrier's expected count includes these arrivals.
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 // Make this thread's generic-proxy shared-memory writes visible to the
 // async proxy (TMA stores, tcgen05.mma operand reads).
 __device__ __forceinline__ void fence_async_smem() {

@@ -77,5 +77,6 @@ def test_apply_rejects_null_operator(so):
     assert so.dctf_apply(None, None, 10, None, None) == 1
     assert so.dctf_apply_f64in(None, None, 10, None, None) == 1
     assert so.dctf_apply_host(None, None, 10, None) == 1
+    assert so.dctf_host_buffer_direct(None, 16) == 0
     assert so.dctf_operator_set_precision(None, 0) == 1
     so.dctf_release_operator(None)        # no-op
