@@ -73,6 +73,12 @@ typedef enum { DCTF_ZERO = 0, DCTF_REPLICATE = 1 } dctf_boundary;
  *  TF32X1    : tcgen05, x and M rounded to TF32 once, one product; about
  *              3 decimal digits, NOT within the 1e-3 coefficient bar (for
  *              comparison).  n = 16.
+ *  BF16X3    : tcgen05, BF16 hi/lo split of x and M (the first two BF16X6
+ *              pieces), hi*hi + hi*lo + lo*hi: the three-term split with
+ *              BF16 pieces, ~16 significant bits, so NOT within the 1e-3
+ *              coefficient bar (max 1-3e-3 on the 16x16 workload; 2e-4 in
+ *              the pixel domain); the cost of F16X3 without its
+ *              |x| < 65504 limit.  n = 16.
  *  KRON_FP32 : the paper's form (Sec. II.B Eq. 11-12, Sec. II.C Eq. 20):
  *              M = sum_t A_t kron B_t with one term per rank of the mask,
  *              applied as sandwich products Y = sum_t A_t X B_t^T in FP32
@@ -88,7 +94,8 @@ typedef enum {
     DCTF_BF16X6 = 2,
     DCTF_TF32X1 = 3,
     DCTF_TF32X3 = 4,
-    DCTF_KRON_FP32 = 5
+    DCTF_KRON_FP32 = 5,
+    DCTF_BF16X3 = 6
 } dctf_precision;
 
 typedef struct dctf_operator dctf_operator;

@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3", "KRON_FP32",
+    "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3", "KRON_FP32", "BF16X3",
     "DctfError", "load", "lib_path", "exported_symbols", "build_operator", "Operator",
     "apply", "apply_f64in", "apply_host", "host_buffer_direct", "apply_pixels", "apply_planar", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
     "version", "IO_F32", "IO_I16", "Group", "group_create", "apply_grouped", "Server",
@@ -24,7 +24,7 @@ ZERO, REPLICATE = 0, 1
 IO_F32, IO_I16 = 0, 1
 APPLY_INPUTS_READY = 1
 MASK_CONVOLUTION, BUILD_KRON = 1, 2
-FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3, KRON_FP32 = 0, 1, 2, 3, 4, 5
+FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3, KRON_FP32, BF16X3 = 0, 1, 2, 3, 4, 5, 6
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ETIMEOUT",
            6: "EUNSUPPORTED"}
 

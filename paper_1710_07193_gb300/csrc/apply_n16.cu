@@ -13,6 +13,8 @@
 //            i + j <= 2                                              (kind::f16, bf16)
 //   TF32X3 : x, M in TF32 hi + lo; hi.lo, lo.hi, hi.hi              (kind::tf32)
 //   TF32X1 : x, M rounded to TF32 once; one product (not exact)     (kind::tf32)
+//   BF16X3 : x, M in BF16 hi + lo; hi.lo, lo.hi, hi.hi (~16 bits,
+//            not exact)                                              (kind::f16, bf16)
 //
 // Tensor-core FP32 accumulation truncates, so the order matters: per K half
 // of 128 inputs, each with its own accumulator, the correction products go
@@ -73,6 +75,12 @@ struct SplitBf16x6 {
 struct SplitTf32x3 {
   static constexpr int kPieces = 2, kImgPieces = 2, kOut = 64, kDBufs = 2, kCorr = 2;
   static constexpr bool kTf32 = true, kBf16 = false;
+  __device__ static constexpr int corr_x(int j) { return j; }
+  __device__ static constexpr int corr_m(int j) { return 1 - j; }
+};
+struct SplitBf16x3 {     // the first two BF16X6 pieces of M
+  static constexpr int kPieces = 2, kImgPieces = 3, kOut = 128, kDBufs = 1, kCorr = 2;
+  static constexpr bool kTf32 = false, kBf16 = true;
   __device__ static constexpr int corr_x(int j) { return j; }
   __device__ static constexpr int corr_m(int j) { return 1 - j; }
 };
@@ -141,6 +149,20 @@ __device__ __forceinline__ void convert_store(const float (&v)[32], uint32_t t_a
       for (int c = 0; c < 32; ++c) lo[c] = tf32_rna(v[c] - __uint_as_float(hi[c]));
       tmem_st32(t_a + 32, lo);
     }
+  } else if constexpr (S::kBf16 && S::kPieces == 2) {
+    // x ~ x0 + x1 (16 of FP32's 24 bits)
+    uint32_t p0[16], p1[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float a0 = v[2 * c], a1 = v[2 * c + 1];
+      const __nv_bfloat162 b0 = __floats2bfloat162_rn(a0, a1);
+      const float2 f0 = __bfloat1622float2(b0);
+      const __nv_bfloat162 b1 = __floats2bfloat162_rn(a0 - f0.x, a1 - f0.y);
+      p0[c] = *reinterpret_cast<const uint32_t *>(&b0);
+      p1[c] = *reinterpret_cast<const uint32_t *>(&b1);
+    }
+    tmem_st16(t_a, p0);
+    tmem_st16(t_a + 16, p1);
   } else if constexpr (S::kBf16) {
     // x = x0 + x1 + x2 exactly (FP32 has 24 bits, each BF16 piece takes 8)
     uint32_t p0[16], p1[16], p2[16];
@@ -478,6 +500,8 @@ cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nb
       return launch<SplitTf32x3>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s);
     case DCTF_TF32X1:
       return launch<SplitTf32x1>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s);
+    case DCTF_BF16X3:
+      return launch<SplitBf16x3>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s);
     default:
       return cudaErrorInvalidValue;
   }

@@ -255,7 +255,7 @@ dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p) {
     op->precision = p;
     return DCTF_OK;
   }
-  if (p < DCTF_FP32_SIMT || p > DCTF_TF32X3)
+  if (p < DCTF_FP32_SIMT || (p > DCTF_TF32X3 && p != DCTF_BF16X3))
     return set_error(DCTF_EINVAL, "unknown precision %d", (int)p);
   if (!tc_supported(op->n, p))
     return set_error(DCTF_EUNSUPPORTED, "precision %d has no kernel for n=%d", (int)p, op->n);

@@ -68,7 +68,8 @@ struct dctf_operator {
   __half *d_f16;            // F16X3 pieces: rows 0..n2-1 hi, n2..2n2-1 lo (sw128)
   __half *d_f16_pix;        // n = 8: F16X3 pieces of the pixel operator G = H K^T
   float *d_Gdc;             // n = 8: G[:, 0] in FP32
-  __nv_bfloat16 *d_bf16;    // n = 16: BF16X6 pieces m0, m1, m2 (3 n2 rows per 64-chunk)
+  __nv_bfloat16 *d_bf16;    // n = 16: BF16 pieces m0, m1, m2 (3 n2 rows per 64-chunk;
+                            //   BF16X3 uses m0, m1)
   uint32_t *d_tf32;         // n = 16: TF32 pieces hi, lo (2 n2 rows per 32-chunk)
   bool kron;                // built with DCTF_BUILD_KRON: Kronecker factors kept
   int krank;                //   number of terms of M = sum_t A_t kron B_t
@@ -99,7 +100,8 @@ cudaError_t launch_apply_simt(const dctf_operator *op, const float *x,
 // F16X3) and apply_n16.cu (n = 16, every split precision)
 inline bool tc_supported(int n, dctf_precision p) {
   if (n == 8) return p == DCTF_F16X3;
-  return n == 16 && (p == DCTF_F16X3 || p == DCTF_BF16X6 || p == DCTF_TF32X1 || p == DCTF_TF32X3);
+  return n == 16 && (p == DCTF_F16X3 || p == DCTF_BF16X6 || p == DCTF_TF32X1 || p == DCTF_TF32X3 ||
+                     p == DCTF_BF16X3);
 }
 cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks,
                              float *y, cudaStream_t s);

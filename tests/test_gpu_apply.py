@@ -46,15 +46,15 @@ def check(y, x32, blocks, w, a, n, boundary, pixels=True):
 
 
 def precisions(n, dctf):
-    """The variants held to the bar for block size n (TF32X1 is not: see
-    test_tf32x1_error_bound)."""
+    """The variants held to the bar for block size n (TF32X1 and BF16X3 are
+    not: see test_tf32x1_error_bound, test_bf16x3_error_bound)."""
     if n == 16:
         return [dctf.FP32_SIMT, dctf.F16X3, dctf.BF16X6, dctf.TF32X3]
     return [dctf.FP32_SIMT, dctf.F16X3] if n == 8 else [dctf.FP32_SIMT]
 
 
 def n16_tc(dctf):
-    return [dctf.F16X3, dctf.BF16X6, dctf.TF32X3, dctf.TF32X1]
+    return [dctf.F16X3, dctf.BF16X6, dctf.TF32X3, dctf.TF32X1, dctf.BF16X3]
 
 
 @pytest.fixture(scope="module")
@@ -158,7 +158,7 @@ def test_other_block_sizes(dctf, n):
 
 def test_split_variants_need_16x16(dctf):
     op = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 8, dctf.ZERO)
-    for p in (dctf.BF16X6, dctf.TF32X1, dctf.TF32X3):
+    for p in (dctf.BF16X6, dctf.TF32X1, dctf.TF32X3, dctf.BF16X3):
         with pytest.raises(dctf.DctfError) as e:
             op.set_precision(p)
         assert e.value.status == 6                          # EUNSUPPORTED
@@ -308,6 +308,36 @@ def test_tf32x1_error_bound(dctf, n16_source, boundary):
     op.release()
 
 
+def bf16x3_bound(m, x):
+    """Bound on |y - M x| for BF16X3 from its arithmetic.  BF16 keeps 8
+    significant bits, so x0 = rn(x) is off by <= 2^-8 |x| and x1 = rn(x - x0)
+    leaves x - x0 - x1 <= 2^-16 |x|; the same holds for M's pieces m0, m1.
+    The three products miss x0 (M - m0 - m1) + x1 (M - m0) + (x - x0 - x1) M,
+    <= 3 (1 + 2^-7) 2^-16 |M_jk x_k|; the truncating FP32 accumulation of 48
+    MMAs per accumulator adds <= 2^-16 sum_k |M_jk x_k|; the DC term is exact
+    to FP32 rounding."""
+    s = np.abs(x[:, 1:]) @ np.abs(m[:, 1:]).T
+    return (3 * (1 + 2.0**-7) + 1) * 2.0**-16 * s + 1e-5 * (1 + np.abs(x[:, :1]) * np.abs(m[:, 0])[None, :])
+
+
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_bf16x3_error_bound(dctf, n16_source, boundary):
+    """BF16X3 (the three-term split with BF16 hi/lo pieces) is not exact:
+    its error stays inside the bound its arithmetic gives and lies well
+    above the exact splits' (so the two-piece variant is what runs)."""
+    _, x = n16_source
+    x = x[:5000]
+    w, a = datagen.large_mask(), (4, 4)
+    op = dctf.build_operator(w, a, 16, boundary)
+    y = run(dctf, op, x, dctf.BF16X3)
+    m = oracle.build_M(w, a, 16, boundary)
+    y_ref = oracle.apply_M(m, x.astype(np.float64))
+    err = np.abs(y - y_ref)
+    assert (err <= bf16x3_bound(m, x.astype(np.float64))).all()
+    assert err.max() > 5e-4
+    op.release()
+
+
 def test_error_table_16x16(dctf, capsys):
     """Max coefficient error vs the FP64 oracle for each arithmetic on the
     16x16 workload's mask (perturbed 9x9 Gaussian, border replication),
@@ -321,8 +351,9 @@ def test_error_table_16x16(dctf, capsys):
     for name in ("FP32_SIMT", "F16X3", "BF16X6", "TF32X3"):
         errs[name] = check(run(dctf, op, x, getattr(dctf, name)), x, blocks, w, a, 16,
                            oracle.REPLICATE)
-    y = run(dctf, op, x, dctf.TF32X1)
-    errs["TF32X1"] = np.abs(y - oracle.apply_M(oracle.build_M(w, a, 16, oracle.REPLICATE),
+    for name in ("TF32X1", "BF16X3"):
+        y = run(dctf, op, x, getattr(dctf, name))
+        errs[name] = np.abs(y - oracle.apply_M(oracle.build_M(w, a, 16, oracle.REPLICATE),
                                                x.astype(np.float64))).max()
     with capsys.disabled():
         print(f"\n16x16 max coefficient error: {errs}")
