@@ -369,9 +369,10 @@ class Server:
         self.handle = h.value
         self._keep = {}
 
-    def submit(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int) -> int:
-        """planes_in/out: host int16 arrays [nblocks][64] (kept alive until wait);
-        qtabs: uint16 [64] per plane."""
+    def prepare(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int):
+        """Marshal one request (argument conversion only) for submit_prepared.
+        planes_in/out: host int16 arrays [nblocks][64] (kept alive until the
+        request is waited for); qtabs: uint16 [64] per plane."""
         r = _Request()
         r.nplanes = len(planes_in)
         keep = [np.ascontiguousarray(mask, dtype=np.float64)]
@@ -386,10 +387,19 @@ class Server:
         r.mh, r.mw = keep[0].shape
         r.anchor[0], r.anchor[1] = anchor
         r.boundary = boundary
+        return (r, keep)
+
+    def submit_prepared(self, prepared) -> int:
+        """One dctf_server_submit call on a request made by prepare()."""
+        r, keep = prepared
         t = ctypes.c_uint64(0)
         _check(load().dctf_server_submit(self.handle, ctypes.addressof(r), ctypes.addressof(t)))
         self._keep[t.value] = keep
         return t.value
+
+    def submit(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int) -> int:
+        """prepare() + submit_prepared()."""
+        return self.submit_prepared(self.prepare(planes_in, planes_out, qtabs, mask, anchor, boundary))
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> None:
         st = load().dctf_server_wait(self.handle, ticket, timeout_ms)
