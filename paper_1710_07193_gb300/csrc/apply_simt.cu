@@ -160,7 +160,13 @@ cudaError_t dispatch(const dctf_operator *op, const Tin *x, int64_t nblocks, flo
                      cudaStream_t s) {
   switch (op->n) {
     case 4:  return launch_cfg<Tin, 16, 128, 16, 16, 8, 2>(op, x, nblocks, y, s);
-    case 8:  return launch_cfg<Tin, 64, 128, 64, 64, 8, 8>(op, x, nblocks, y, s);
+    case 8:
+      // fewer blocks than 128-block tiles can spread over the SMs (the
+      // 256 x 256 workload has 1,024): 16-block tiles, 8x the CTAs.  Each
+      // output sums the same K chunks in the same order, so the bits match.
+      if (nblocks < (int64_t)128 * sm_count(op->device))
+        return launch_cfg<Tin, 64, 16, 64, 64, 2, 4>(op, x, nblocks, y, s);
+      return launch_cfg<Tin, 64, 128, 64, 64, 8, 8>(op, x, nblocks, y, s);
     case 16: return launch_cfg<Tin, 256, 32, 128, 64, 4, 8>(op, x, nblocks, y, s);
   }
   return cudaErrorInvalidValue;

@@ -76,6 +76,22 @@ def test_ragged_block_counts(dctf, ragged_source, nb, prec):
     assert op.status() == 0
 
 
+def test_simt_tile_configs_agree(dctf, ragged_source):
+    """Below 128 x (SM count) blocks the CUDA-core kernel uses 16-block
+    tiles; each output sums the same terms in the same order, so both tile
+    shapes give the same bits."""
+    blocks, x = ragged_source
+    w, a = datagen.headline_mask(), (1, 3)
+    op = dctf.build_operator(w, a, 8, dctf.REPLICATE)
+    cut = 128 * torch.cuda.get_device_properties(0).multi_processor_count
+    assert x.shape[0] > cut
+    y_big = run(dctf, op, x[:cut], dctf.FP32_SIMT)           # 128-block tiles
+    y_small = run(dctf, op, x[:cut - 1], dctf.FP32_SIMT)     # 16-block tiles
+    assert np.array_equal(y_big[:cut - 1], y_small)
+    check(y_small[:2000], x[:2000], blocks[:2000], w, a, 8, oracle.REPLICATE)
+    op.release()
+
+
 def test_small_workload_fp64_coefficients(dctf):
     """256x256, 3x3 Gaussian sigma=1, zero padding, FP64 coefficients in."""
     job = datagen.small_job()
