@@ -368,6 +368,17 @@ def run_workloads(lib, torch, reps: int):
                                 "autotuned": {"ctas": grid, "tile_rows": rows},
                                 "one_launch_GBps": nb_total * BYTES_PER_BLOCK / (tg / 1e3) / 1e9}
     grp.destroy()
+    # the same 64 images to filtered uint8 pixels in one persistent launch
+    pims = [torch.empty(j.image.shape, dtype=torch.uint8, device=dev) for j in jobs]
+    gpx = lib.group_create_pixels([(o, xi, j.image.shape[0], j.image.shape[1], im)
+                                   for (o, xi, _, _), j, im in zip(items, jobs, pims)])
+    gpx.tune(reps=5)
+    tp = graph_time_ms(torch, lambda s: gpx.launch(stream=s), reps)
+    out["grouped_64_images"]["pixels_one_launch_us"] = 1e3 * tp
+    out["grouped_64_images"]["pixels_one_launch_GBps"] = (nb_total * PIXEL_BYTES_PER_BLOCK
+                                                          / (tp / 1e3) / 1e9)
+    gpx.destroy()
+    del pims
     for o, *_ in items:
         o.release()
     del items
@@ -575,6 +586,20 @@ def run_dctf(args):
                     "frac_of_measured_hbm": px_gbps / measured_peaks()[0],
                     "bytes_per_block": PIXEL_BYTES_PER_BLOCK,
                     "kernel": "apply_group_kernel<float,4,1,false,true> (pixel epilogue)"}
+    # the same, for the ROTATE distinct 4096^2 inputs in ONE persistent
+    # launch (a stream of frames): the per-launch fill and drain are paid once
+    gpx = lib.group_create_pixels([(ops[0], xs[i], h, w, imgs[i]) for i in range(ROTATE)])
+    gpx.tune(reps=5)
+    gpx.launch(stream=None)
+    torch.cuda.synchronize()
+    g_ms = graph_time_ms(torch, lambda s: gpx.launch(stream=s), 20)
+    g_gbps = PIXEL_BYTES_PER_BLOCK * nb * ROTATE / (g_ms / 1e3) / 1e9
+    fused_pixels["grouped"] = {"images": ROTATE, "us_per_launch": 1e3 * g_ms,
+                               "us_per_image": 1e3 * g_ms / ROTATE, "GBps": g_gbps,
+                               "frac_of_measured_hbm": g_gbps / measured_peaks()[0],
+                               "kernel": "apply_group_kernel<float,4,2,true,1> (pixel epilogue, "
+                                         "items in global memory)"}
+    gpx.destroy()
     del imgs
     # image-plane coefficient layout (dctf_apply_planar): the same
     # coefficients rearranged as an h x w plane, 512 B per block

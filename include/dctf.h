@@ -306,6 +306,32 @@ void dctf_group_destroy(dctf_group *g);
 dctf_status dctf_apply_grouped(const dctf_group_item *items, int nitems,
                                dctf_io io, dctf_stream_t stream);
 
+/* Grouped fused pixel output: many images, each with its own 8x8 operator,
+ * from block-DCT coefficients to filtered uint8 pixels in ONE persistent
+ * launch (dctf_apply_pixels per item: the pixel operator H K^T, Eq. 3 after
+ * Eq. 7, round half away from zero and saturate, Sec. III).  Each item:
+ *   coeffs : device [ (height/8) * (width/8) ][64] FP32, raster block order,
+ *            16-byte aligned (caller-owned, read only);
+ *   image  : device uint8, `height` rows of `pitch` bytes, 8-byte aligned;
+ *            only the height x width pixels are written; must not overlap
+ *            coeffs;
+ *   height, width: positive multiples of 8; pitch >= width, multiple of 8.
+ * The group is used like a coefficient group: dctf_group_launch (graph-
+ * capturable), dctf_group_tune (needs no in-place care: inputs are never
+ * written), dctf_group_config, dctf_group_status, dctf_group_destroy.
+ * EINVAL on a bad item (nothing is allocated), EUNSUPPORTED for an operator
+ * that is not 8x8. */
+typedef struct {
+    const dctf_operator *op;  /* n = 8 operator (kept alive by the caller)     */
+    const float *coeffs;
+    int height, width;
+    uint8_t *image;
+    int64_t pitch;            /* bytes per image row                          */
+} dctf_pixel_item;
+
+dctf_status dctf_group_create_pixels(const dctf_pixel_item *items, int nitems,
+                                     dctf_group **out);
+
 /* ---------------------------------------------------------------------
  * Serving: a continuous-batching request loop for JPEG-style quantised
  * planes (the library's serving form of the per-block filter; the paper has

@@ -17,7 +17,8 @@ __all__ = [
     "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3", "KRON_FP32", "BF16X3",
     "DctfError", "load", "lib_path", "exported_symbols", "build_operator", "Operator",
     "apply", "apply_f64in", "apply_host", "host_buffer_direct", "apply_pixels", "apply_planar", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
-    "version", "IO_F32", "IO_I16", "Group", "group_create", "apply_grouped", "Server",
+    "version", "IO_F32", "IO_I16", "Group", "group_create", "group_create_pixels", "apply_grouped",
+    "Server",
 ]
 
 ZERO, REPLICATE = 0, 1
@@ -56,6 +57,7 @@ _SIGS = {
     "dctf_inverse_dct_u8": (_i32, [_vp, _i32, _i32, _i32, _vp, _i64, _vp]),
     "dctf_build_matrix_noalloc": (_i32, [_vp, _i32, _i32, _vp, _i32, _i32, _vp, _vp, _vp]),
     "dctf_group_create": (_i32, [_vp, _i32, _i32, _vp]),
+    "dctf_group_create_pixels": (_i32, [_vp, _i32, _vp]),
     "dctf_group_launch": (_i32, [_vp, _vp]),
     "dctf_group_tune": (_i32, [_vp, _vp, _i32]),
     "dctf_group_config": (_i32, [_vp, _vp, _vp]),
@@ -316,6 +318,24 @@ def group_create(items, io: int = IO_F32) -> Group:
     arr = _items_array(items)
     h = ctypes.c_void_p(0)
     _check(load().dctf_group_create(ctypes.addressof(arr), len(items), io, ctypes.addressof(h)))
+    return Group(h.value, [it[0] for it in items])
+
+
+class _PixelItem(ctypes.Structure):
+    _fields_ = [("op", _vp), ("coeffs", _vp), ("height", _i32), ("width", _i32),
+                ("image", _vp), ("pitch", _i64)]
+
+
+def group_create_pixels(items) -> Group:
+    """items: sequence of (op, coeffs, height, width, image[, pitch]): fused
+    pixel output for every item in one persistent launch."""
+    arr = (_PixelItem * max(1, len(items)))()
+    for i, it in enumerate(items):
+        op, x, h, w, img = it[:5]
+        pitch = it[5] if len(it) > 5 and it[5] is not None else w
+        arr[i] = _PixelItem(op.handle, _ptr(x), int(h), int(w), _ptr(img), int(pitch))
+    h = ctypes.c_void_p(0)
+    _check(load().dctf_group_create_pixels(ctypes.addressof(arr), len(items), ctypes.addressof(h)))
     return Group(h.value, [it[0] for it in items])
 
 

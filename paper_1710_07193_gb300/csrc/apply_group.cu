@@ -801,6 +801,17 @@ cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int he
                                                      err, s, pdl);
 }
 
+cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int64_t total_halves,
+                                      int grid, int max_take, uint32_t *err, cudaStream_t s) {
+  if (total_halves <= 0) return cudaSuccess;
+  int64_t g = grid > 0 ? grid : 0;
+  if (g > total_halves) g = total_halves;
+  if (g < 1) g = 1;
+  static const GroupItem kEmpty = {};
+  return launch_cfg<float, 4, 2, true, kModePixels>(d_items, kEmpty, nitems, total_halves, (int)g,
+                                                    max_take == 1 ? 1 : 2, 0, err, s, false);
+}
+
 cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halves, int grid,
                                      uint32_t *err, cudaStream_t s) {
   if (total_halves <= 0) return cudaSuccess;

@@ -63,6 +63,12 @@ cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int he
 cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halves, int grid,
                                      uint32_t *err, cudaStream_t s);
 
+// Fused pixel output for many items (descriptors in global memory, each
+// filled as for launch_apply_pixels): one persistent launch, contiguous
+// schedule, two operator slots.
+cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int64_t total_halves,
+                                      int grid, int max_take, uint32_t *err, cudaStream_t s);
+
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,
                                uint32_t *err, cudaStream_t s, bool pdl = false);

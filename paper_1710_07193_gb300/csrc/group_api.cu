@@ -1,7 +1,9 @@
 // Grouped apply: C ABI, launch plans and the autotuner.
 //
 // A group is a list of (operator, input, output, quantisation tables)
-// items run by one persistent launch of apply_group_kernel.  Creating a
+// items run by one persistent launch of apply_group_kernel; a pixel group's
+// items are (operator, coefficients, uint8 image) for the fused pixel
+// output.  Creating a
 // group encodes every item's TMA tensor maps once and uploads the
 // descriptors; launching it is then a single kernel launch with no host work,
 // so it can be captured in a CUDA graph and replayed.
@@ -25,6 +27,7 @@ struct dctf_group {
   int device;
   int nitems;
   bool i16;
+  bool pixels;     // items write uint8 images (fused pixel output)
   int64_t total_halves;
   dctf::GroupItem *d_items;
   uint32_t *d_err;
@@ -37,12 +40,13 @@ namespace dctf {
 namespace {
 
 struct TuneKey {
-  bool i16;
+  int kind;         // 0: FP32 coefficients, 1: int16, 2: pixels
   int size_class;   // floor(log2(total halves))
   bool operator<(const TuneKey &o) const {
-    return i16 != o.i16 ? i16 < o.i16 : size_class < o.size_class;
+    return kind != o.kind ? kind < o.kind : size_class < o.size_class;
   }
 };
+int kind_of(const dctf_group *g) { return g->pixels ? 2 : g->i16 ? 1 : 0; }
 struct TuneVal { int grid_num, grid_den, max_take; };
 
 std::mutex g_tune_mu;
@@ -105,9 +109,107 @@ dctf_status fill_items(const dctf_group_item *items, int nitems, dctf_io io,
   return DCTF_OK;
 }
 
+dctf_status check_pixel_items(const dctf_pixel_item *items, int nitems) {
+  if (nitems < 0 || (nitems > 0 && items == nullptr))
+    return set_error(DCTF_EINVAL, "bad item list");
+  for (int i = 0; i < nitems; ++i) {
+    const dctf_pixel_item &it = items[i];
+    if (it.op == nullptr) return set_error(DCTF_EINVAL, "item %d: operator is NULL", i);
+    if (it.op->n != 8 || it.op->d_f16_pix == nullptr)
+      return set_error(DCTF_EUNSUPPORTED, "item %d: the fused pixel apply needs an 8x8 operator", i);
+    if (it.coeffs == nullptr || it.image == nullptr)
+      return set_error(DCTF_EINVAL, "item %d: NULL buffer", i);
+    if (it.height <= 0 || it.width <= 0 || it.height % 8 || it.width % 8)
+      return set_error(DCTF_EINVAL, "item %d: image %dx%d: sides must be positive multiples of 8",
+                       i, it.height, it.width);
+    if (it.pitch < it.width || it.pitch % 8)
+      return set_error(DCTF_EINVAL, "item %d: pitch must be >= width and a multiple of 8", i);
+    if (!aligned16(it.coeffs) || (reinterpret_cast<uintptr_t>(it.image) & 7))
+      return set_error(DCTF_EINVAL, "item %d: coeffs must be 16-byte, image 8-byte aligned", i);
+    const int64_t nb = (int64_t)(it.height / 8) * (it.width / 8);
+    if (nb > ((int64_t)1 << 31) - 128) return set_error(DCTF_EINVAL, "item %d: image too large", i);
+    const char *a = reinterpret_cast<const char *>(it.coeffs);
+    const char *b = reinterpret_cast<const char *>(it.image);
+    const size_t la = (size_t)nb * 64 * sizeof(float);
+    const size_t lb = (size_t)(it.height - 1) * it.pitch + it.width;
+    if (a < b + lb && b < a + la)
+      return set_error(DCTF_EINVAL, "item %d: coefficients and image overlap", i);
+  }
+  return DCTF_OK;
+}
+
+dctf_status fill_pixel_items(const dctf_pixel_item *items, int nitems,
+                             std::vector<GroupItem> *out, int64_t *total) {
+  out->resize(nitems > 0 ? nitems : 1);
+  int64_t h = 0;
+  for (int i = 0; i < nitems; ++i) {
+    const dctf_pixel_item &it = items[i];
+    GroupItem &gi = (*out)[i];
+    const int64_t nb = (int64_t)(it.height / 8) * (it.width / 8);
+    // (the coefficient output map is not used: pointed at the input)
+    cudaError_t e = fill_group_item(&gi, it.op, it.coeffs, const_cast<float *>(it.coeffs), nb,
+                                    false, nullptr, nullptr);
+    if (e != cudaSuccess) return cuda_error(e, "tensor map encode");
+    gi.pieces = it.op->d_f16_pix;
+    gi.mdc = it.op->d_Gdc;
+    gi.img = it.image;
+    gi.pitch = it.pitch;
+    gi.bw = it.width / 8;
+    gi.half_begin = h;
+    h += (nb + 63) / 64;
+  }
+  *total = h;
+  return DCTF_OK;
+}
+
 cudaError_t launch(const dctf_group *g, int grid, int max_take, cudaStream_t s) {
+  if (g->pixels)
+    return launch_apply_group_pixels(g->d_items, g->nitems, g->total_halves, grid, max_take,
+                                     g->d_err, s);
   return launch_apply_group(g->d_items, nullptr, g->nitems, g->total_halves, g->i16, grid,
                             max_take, g->d_err, s);
+}
+
+// Uploads the descriptors and picks the launch parameters (the autotuner's
+// cached choice for this kind and size class, else one CTA per SM and
+// 128-row tiles).
+dctf_status make_group(const std::vector<GroupItem> &host, int nitems, int64_t total, bool i16,
+                       bool pixels, bool in_place, dctf_group **out) {
+  dctf_group *g = new (std::nothrow) dctf_group();
+  if (g == nullptr) return set_error(DCTF_ENOMEM, "host allocation failed");
+  g->nitems = nitems;
+  g->i16 = i16;
+  g->pixels = pixels;
+  g->total_halves = total;
+  g->in_place = in_place;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_items, host.size() * sizeof(GroupItem) + 256);
+  if (e == cudaSuccess) {
+    g->d_err = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(g->d_items) +
+                                            host.size() * sizeof(GroupItem));
+    e = cudaMemcpy(g->d_items, host.data(), host.size() * sizeof(GroupItem),
+                   cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, 256);
+  if (e != cudaSuccess) {
+    if (g->d_items) cudaFree(g->d_items);
+    delete g;
+    return cuda_error(e, "group descriptors");
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(TuneKey{kind_of(g), size_class(total)});
+    const int sms = sm_count(g->device);
+    if (it != g_tune_cache.end()) {
+      g->grid = std::max(1, sms * it->second.grid_num / it->second.grid_den);
+      g->max_take = it->second.max_take;
+    } else {
+      g->grid = 0;
+      g->max_take = 2;
+    }
+  }
+  *out = g;
+  return DCTF_OK;
 }
 
 }  // namespace
@@ -127,41 +229,22 @@ dctf_status dctf_group_create(const dctf_group_item *items, int nitems, dctf_io 
   int64_t total = 0;
   st = fill_items(items, nitems, io, &host, &total);
   if (st != DCTF_OK) return st;
-  dctf_group *g = new (std::nothrow) dctf_group();
-  if (g == nullptr) return set_error(DCTF_ENOMEM, "host allocation failed");
-  g->nitems = nitems;
-  g->i16 = io == DCTF_IO_I16;
-  g->total_halves = total;
+  bool in_place = false;
   for (int i = 0; i < nitems; ++i)
-    if (items[i].nblocks > 0 && items[i].in == items[i].out) g->in_place = true;
-  cudaError_t e = cudaGetDevice(&g->device);
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_items, host.size() * sizeof(GroupItem) + 256);
-  if (e == cudaSuccess) {
-    g->d_err = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(g->d_items) +
-                                            host.size() * sizeof(GroupItem));
-    e = cudaMemcpy(g->d_items, host.data(), host.size() * sizeof(GroupItem),
-                   cudaMemcpyHostToDevice);
-  }
-  if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, 256);
-  if (e != cudaSuccess) {
-    if (g->d_items) cudaFree(g->d_items);
-    delete g;
-    return cuda_error(e, "group descriptors");
-  }
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tune_cache.find(TuneKey{g->i16, size_class(total)});
-    const int sms = sm_count(g->device);
-    if (it != g_tune_cache.end()) {
-      g->grid = std::max(1, sms * it->second.grid_num / it->second.grid_den);
-      g->max_take = it->second.max_take;
-    } else {
-      g->grid = 0;
-      g->max_take = 2;
-    }
-  }
-  *out = g;
-  return DCTF_OK;
+    if (items[i].nblocks > 0 && items[i].in == items[i].out) in_place = true;
+  return make_group(host, nitems, total, io == DCTF_IO_I16, false, in_place, out);
+}
+
+dctf_status dctf_group_create_pixels(const dctf_pixel_item *items, int nitems, dctf_group **out) {
+  if (out == nullptr) return set_error(DCTF_EINVAL, "out is NULL");
+  *out = nullptr;
+  dctf_status st = check_pixel_items(items, nitems);
+  if (st != DCTF_OK) return st;
+  std::vector<GroupItem> host;
+  int64_t total = 0;
+  st = fill_pixel_items(items, nitems, &host, &total);
+  if (st != DCTF_OK) return st;
+  return make_group(host, nitems, total, false, true, false, out);
 }
 
 dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream) {
@@ -214,7 +297,7 @@ dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps) {
   g->grid = std::max(1, sms * best_v.grid_num / best_v.grid_den);
   g->max_take = best_v.max_take;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_cache[TuneKey{g->i16, size_class(g->total_halves)}] = best_v;
+  g_tune_cache[TuneKey{kind_of(g), size_class(g->total_halves)}] = best_v;
   return DCTF_OK;
 }
 

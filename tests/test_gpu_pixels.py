@@ -115,3 +115,67 @@ def test_pixels_argument_checks(dctf):
     assert e.value.status == 6
     op8.release()
     op16.release()
+
+
+def test_grouped_pixels_match_single_launches_and_oracle(dctf):
+    """Many images, each with its own operator, to uint8 in one persistent
+    launch: every image equals its own dctf_apply_pixels launch bit for bit
+    (same arithmetic) and the oracle's spatial filter outside the tie band;
+    pitch padding stays untouched; tuning and CUDA-graph replay give the
+    same images."""
+    jobs = datagen.grouped_jobs(count=16, scale=0.2)
+    items = []
+    for i, job in enumerate(jobs):
+        h, w = job.image.shape
+        x = oracle.dct2_blocks(oracle.image_to_blocks(job.image, 8)).astype(np.float32)
+        pitch = w + 8 * (i % 3)
+        img = torch.full((h, pitch), 77, dtype=torch.uint8, device="cuda")
+        op = dctf.build_operator(job.mask, job.anchor, 8, job.boundary)
+        items.append((op, torch.from_numpy(x).cuda(), h, w, img, pitch))
+    g = dctf.group_create_pixels(items)
+    g.launch()
+    torch.cuda.synchronize()
+    assert g.status() == 0
+    singles = []
+    for (op, xd, h, w, img, pitch), job in zip(items, jobs):
+        u8 = img.cpu().numpy()
+        assert (u8[:, w:] == 77).all()
+        check_image(u8, job.image, job.mask, job.anchor, job.boundary)
+        one = torch.full_like(img, 77)
+        dctf.apply_pixels(op, xd, h, w, one, pitch)
+        torch.cuda.synchronize()
+        assert torch.equal(one, img)
+        singles.append(one)
+    g.tune(reps=2)
+    for it in items:
+        it[4].fill_(0)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+        g.launch(stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for it, one in zip(items, singles):
+        assert torch.equal(it[4][:, :it[3]], one[:, :it[3]])
+    g.destroy()
+    for it in items:
+        it[0].release()
+
+
+def test_grouped_pixels_reject_bad_items(dctf):
+    op = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 8, dctf.ZERO)
+    op16 = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 16, dctf.ZERO)
+    x = torch.zeros((16, 64), device="cuda")
+    img = torch.zeros((32, 32), dtype=torch.uint8, device="cuda")
+    with pytest.raises(dctf.DctfError) as e:
+        dctf.group_create_pixels([(op16, x, 32, 32, img)])
+    assert e.value.status == 6                              # EUNSUPPORTED
+    for bad in ([(op, x, 32, 30, img)],                      # width not a multiple of 8
+                [(op, x, 32, 32, img, 24)],                  # pitch < width
+                [(op, x, 0, 32, img)],                       # empty image
+                [(op, x[:, 1:], 32, 32, img)]):              # misaligned coefficients
+        with pytest.raises(dctf.DctfError) as e:
+            dctf.group_create_pixels(bad)
+        assert e.value.status == 1                          # EINVAL
+    op.release()
+    op16.release()
