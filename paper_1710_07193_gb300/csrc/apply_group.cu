@@ -49,9 +49,11 @@
 //    memory with coalesced 16-byte stores.  Every byte crosses the host link
 //    once each way, with no device buffer and no copy engine.
 //
-// Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM
-// allocator, warp 3 slot loader, warps 4-7 converter (thread = tile row),
-// warps 8-11 epilogue (each warp stores its own 32 rows).  TMEM holds a ring
+// Roles (384 threads; 512 in the pixel mode): warp 0 TMA producer, warp 1
+// MMA issuer, warp 2 TMEM allocator, warp 3 slot loader, warps 4-7
+// converter (thread = tile row), warps 8-11 epilogue (each warp stores its
+// own 32 rows; the pixel mode adds warps 12-15, each pair of warps of a
+// lane quarter splitting a block's pixel rows).  TMEM holds a ring
 // of four [A_hi 32 | A_lo 32 | D 64] column buffers, so the MMA can run up to
 // four tiles ahead of the epilogue, which frees its buffer right after one
 // paired TMEM load.  Every wait is bounded (see sm100_ptx.cuh); waits in
@@ -65,7 +67,6 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kThreads = 384;
 constexpr int kTile = 128;
 constexpr int kHalf = 64;
 constexpr int kN2 = 64;
@@ -238,8 +239,14 @@ __device__ __forceinline__ uint32_t pixel_u8(float p) {
 // run on the same SMs while this kernel streams.
 enum : int { kModeBlocks = 0, kModePixels = 1, kModePlanar = 2, kModeHost = 3 };
 
+// The pixel mode runs eight epilogue warps (two per TMEM lane quarter, each
+// taking half of a block's pixel rows): its per-tile epilogue (64 roundings
+// and packings a block) bounds it.  Its 512 threads get 128 registers each.
+__host__ __device__ constexpr int epi_warps(int mode) { return mode == kModePixels ? 8 : 4; }
+__host__ __device__ constexpr int block_threads(int mode) { return 256 + 32 * epi_warps(mode); }
+
 template <typename IoT, int S, int NS, bool kGroup, int kMode>
-__global__ void __maxnreg__(sizeof(IoT) == 4 ? 152 : 168)
+__global__ void __maxnreg__(kMode == kModePixels ? 128 : sizeof(IoT) == 4 ? 152 : 168)
 apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__ GroupItem single,
                    int nitems, int64_t total_halves, int max_take, int interleaved,
                    uint32_t *__restrict__ err) {
@@ -273,10 +280,14 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       mbar_init(&empty_in[s], 128);
     }
     for (int b = 0; b < kBufs; ++b) {
-      mbar_init(&a_full[b], 128); mbar_init(&mma_done[b], 1); mbar_init(&d_empty[b], 128);
+      mbar_init(&a_full[b], 128); mbar_init(&mma_done[b], 1);
+      mbar_init(&d_empty[b], 32 * epi_warps(kMode));
     }
     for (int r = 0; r < kDcRing; ++r) mbar_init(&dc_full[r], 128);
-    for (int k = 0; k < NS; ++k) { mbar_init(&slot_full[k], 1); mbar_init(&slot_empty[k], 257); }
+    for (int k = 0; k < NS; ++k) {   // released by the converter, the epilogue and the MMA
+      mbar_init(&slot_full[k], 1);
+      mbar_init(&slot_empty[k], 128 + 32 * epi_warps(kMode) + 1);
+    }
     *s_abort = 0;
     mbar_fence_init();
   }
@@ -498,7 +509,7 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
     }
   } else if (warp >= 8) {
     // ---------------------------------------------------------- epilogue
-    const int row = tid - 256, wr = warp & 3, r32 = lane;
+    const int wr = warp & 3, row = wr * 32 + lane, r32 = lane;
     const uint32_t lane_base = (uint32_t)(wr * 32) << 16;
     // Under programmatic dependent launch the loads above may run while the
     // previous kernel on the stream finishes; no output is written before
@@ -514,6 +525,59 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         break;
       if (!warp_wait_bounded(&mma_done[b], pb, s_abort, err, kRoleEpi | (it << 8))) break;
       tc_fence_after();
+      if constexpr (kMode == kModePixels) {
+        // warp 8 + 4 hc + wr: TMEM lanes 32 wr.. (its blocks), output columns
+        // 32 hc .. 32 hc + 31, i.e. pixel rows 4 hc .. 4 hc + 3 of each block
+        const int hc = (warp - 8) >> 2;
+        float px[32];
+        {
+          uint32_t d[32];
+          tmem_ld32(tmem + lane_base + b * 128 + 64 + 32 * hc, d);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) px[c] = __uint_as_float(d[c]);
+        }
+        // the DC value is read before D[b] is released (see below)
+        if (!warp_wait_bounded(&dc_full[r], pr, s_abort, err, kRoleEpi | (it << 8))) break;
+        const float x0 = s_dc[r * kTile + row];
+        tc_fence_before();
+        mbar_arrive(&d_empty[b]);
+        const GroupItem &gi = items[t.item];
+        const float out_scale = gi.out_scale;
+        const float4 *mdc4 =
+            reinterpret_cast<const float4 *>(s_slot + k * kSlotBytes + kSlotPieces) + 8 * hc;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 md = mdc4[u];
+          px[4 * u] = fmaf(px[4 * u], out_scale, md.x * x0);
+          px[4 * u + 1] = fmaf(px[4 * u + 1], out_scale, md.y * x0);
+          px[4 * u + 2] = fmaf(px[4 * u + 2], out_scale, md.z * x0);
+          px[4 * u + 3] = fmaf(px[4 * u + 3], out_scale, md.w * x0);
+        }
+        // block bk of the item covers image rows 8 (bk / bw) + 0..7 and
+        // columns 8 (bk % bw) + 0..7; its pixel (i, j) is output i * 8 + j.
+        // The lanes of a warp hold consecutive blocks, so each row's 8-byte
+        // stores of a warp are contiguous.
+        const int64_t bk = (int64_t)t.row0 + row;
+        if (row < t.rows && bk < gi.nblocks) {
+          const int64_t by = bk / gi.bw, bx = bk - by * gi.bw;
+          uint8_t *dst = gi.img + (by * 8 + 4 * hc) * gi.pitch + bx * 8;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            uint32_t w[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float *a = px + 8 * i + 4 * h;
+              // bytes b0..b3 into one word (PRMT: low bytes of four words)
+              w[h] = __byte_perm(__byte_perm(pixel_u8(a[0]), pixel_u8(a[1]), 0x0040),
+                                 __byte_perm(pixel_u8(a[2]), pixel_u8(a[3]), 0x0040), 0x5410);
+            }
+            *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
+          }
+        }
+        if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's G[:,0]
+        ++it;
+        continue;
+      }
       float acc[64];
       {
         uint32_t d0[32], d1[32];
@@ -542,32 +606,6 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         acc[4 * u + 1] = fmaf(acc[4 * u + 1], out_scale, md.y * x0);
         acc[4 * u + 2] = fmaf(acc[4 * u + 2], out_scale, md.z * x0);
         acc[4 * u + 3] = fmaf(acc[4 * u + 3], out_scale, md.w * x0);
-      }
-      if constexpr (kMode == kModePixels) {
-        // block b of the item covers image rows 8 (b / bw) + 0..7 and columns
-        // 8 (b % bw) + 0..7; its pixel (i, j) is output i * 8 + j.  The lanes
-        // of a warp hold consecutive blocks, so each row's 8-byte stores of a
-        // warp are contiguous.
-        const int64_t b = (int64_t)t.row0 + row;
-        if (row < t.rows && b < gi.nblocks) {
-          const int64_t by = b / gi.bw, bx = b - by * gi.bw;
-          uint8_t *dst = gi.img + by * 8 * gi.pitch + bx * 8;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            uint32_t w[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float *a = acc + 8 * i + 4 * h;
-              // bytes b0..b3 into one word (PRMT: low bytes of four words)
-              w[h] = __byte_perm(__byte_perm(pixel_u8(a[0]), pixel_u8(a[1]), 0x0040),
-                                 __byte_perm(pixel_u8(a[2]), pixel_u8(a[3]), 0x0040), 0x5410);
-            }
-            *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
-          }
-        }
-        if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's G[:,0]
-        ++it;
-        continue;
       }
       const bool store = wr * 32 < t.rows;
       uint8_t *slab = s_out + o * L::kStageBytes + wr * L::kSlabBytes;
@@ -716,7 +754,7 @@ cudaError_t launch_cfg(const GroupItem *d_items, const GroupItem &single, int ni
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(block_threads(kMode));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
