@@ -94,11 +94,15 @@ apply_kron_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t nb
   constexpr int H = N / 2;                // threads per block
   constexpr int BPC = kThreads / H;       // blocks per pass
   constexpr int LD = N + 4;               // padded row (16-byte aligned, fewer bank conflicts)
+  // one block's U, padded by 4 floats: N * LD is a multiple of 32 banks, so
+  // unpadded the blocks of a warp would read their U rows from the same
+  // banks (4-way conflicts at N = 16 on every 16-byte load)
+  constexpr int UB = N * LD + 4;
   extern __shared__ __align__(16) float smem_f[];
   float *sA = smem_f;                     // [rank][N][LD]
   float *sB = sA + rank * N * LD;         // [rank][N][N]
-  float *sU = sB + rank * N * N;          // [BPC][N][LD]
-  float *sDc = sU + BPC * N * LD;         // [N * N]: M[:, 0]
+  float *sU = sB + rank * N * N;          // [BPC][UB]
+  float *sDc = sU + BPC * UB;             // [N * N]: M[:, 0]
   for (int e = threadIdx.x; e < rank * N * N; e += kThreads) {
     const int t = e / (N * N), r = (e / N) % N, c = e % N;
     sA[(t * N + r) * LD + c] = A[e];
@@ -107,7 +111,7 @@ apply_kron_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t nb
   for (int e = threadIdx.x; e < N * N; e += kThreads) sDc[e] = Mdc[e];
   __syncthreads();
   const int lb = threadIdx.x / H, i = threadIdx.x % H;   // rows i and i + H
-  float *u_blk = sU + lb * N * LD;
+  float *u_blk = sU + lb * UB;
   for (int64_t b0 = (int64_t)blockIdx.x * BPC; b0 < nblocks; b0 += (int64_t)gridDim.x * BPC) {
     const int64_t b = b0 + lb;
     const bool live = b < nblocks;
@@ -201,9 +205,9 @@ apply_kron_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t nb
 template <int N>
 cudaError_t launch_apply(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
                          cudaStream_t s) {
-  constexpr int BPC = kThreads / (N / 2), LD = N + 4;
+  constexpr int BPC = kThreads / (N / 2), LD = N + 4, UB = N * LD + 4;
   const int smem =
-      (op->krank * N * LD + op->krank * N * N + BPC * N * LD + N * N) * (int)sizeof(float);
+      (op->krank * N * LD + op->krank * N * N + BPC * UB + N * N) * (int)sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(apply_kron_kernel<N>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
