@@ -228,10 +228,12 @@ struct TileWalk {
 // the low mantissa bits.  (Rounding and float-to-integer conversion
 // instructions run on the slower XU pipe, which made the pixel epilogue
 // the bottleneck of the fused kernel.)  A value within one FP32 ulp below
-// a .5 boundary may round up: inside the 1e-4 tie band.
-__device__ __forceinline__ uint32_t pixel_u8(float p) {
+// a .5 boundary may round up: inside the 1e-4 tie band.  The pixel is the
+// low byte of the result (the higher bits hold the exponent of 2^23); the
+// caller packs low bytes with PRMT, so no mask is needed.
+__device__ __forceinline__ uint32_t pixel_u8_low_byte(float p) {
   const float c = fminf(fmaxf(p, 0.f), 255.f) + 0.5f;
-  return __float_as_uint(__fadd_rz(c, 8388608.0f)) & 0xffu;
+  return __float_as_uint(__fadd_rz(c, 8388608.0f));
 }
 
 // FP32 I/O: at most 152 registers a thread (58,368 of the SM's 65,536 for 384
@@ -557,10 +559,11 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         // columns 8 (bk % bw) + 0..7; its pixel (i, j) is output i * 8 + j.
         // The lanes of a warp hold consecutive blocks, so each row's 8-byte
         // stores of a warp are contiguous.
-        const int64_t bk = (int64_t)t.row0 + row;
+        // 32-bit block coordinates: an item has fewer than 2^31 blocks
+        const int bk = t.row0 + row, bw = (int)gi.bw;
         if (row < t.rows && bk < gi.nblocks) {
-          const int64_t by = bk / gi.bw, bx = bk - by * gi.bw;
-          uint8_t *dst = gi.img + (by * 8 + 4 * hc) * gi.pitch + bx * 8;
+          const int by = bk / bw, bx = bk - by * bw;
+          uint8_t *dst = gi.img + ((int64_t)by * 8 + 4 * hc) * gi.pitch + (int64_t)bx * 8;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             uint32_t w[2];
@@ -568,8 +571,9 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
             for (int h = 0; h < 2; ++h) {
               const float *a = px + 8 * i + 4 * h;
               // bytes b0..b3 into one word (PRMT: low bytes of four words)
-              w[h] = __byte_perm(__byte_perm(pixel_u8(a[0]), pixel_u8(a[1]), 0x0040),
-                                 __byte_perm(pixel_u8(a[2]), pixel_u8(a[3]), 0x0040), 0x5410);
+              w[h] = __byte_perm(
+                  __byte_perm(pixel_u8_low_byte(a[0]), pixel_u8_low_byte(a[1]), 0x0040),
+                  __byte_perm(pixel_u8_low_byte(a[2]), pixel_u8_low_byte(a[3]), 0x0040), 0x5410);
             }
             *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
           }
