@@ -71,6 +71,9 @@ static __device__ __noinline__ bool wait_bounded_ns(uint64_t *bar, uint32_t pari
 static __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity,
                                                     volatile int *abort, uint32_t *err,
                                                     uint32_t code) {
+  // fast path inline (the phase is often complete already); the polling
+  // loop with its time limit is an out-of-line call
+  if (mbar_try_wait(bar, parity)) return true;
   return wait_bounded_ns(bar, parity, abort, err, code, kWaitLimitNs);
 }
 
