@@ -45,7 +45,7 @@ ROTATE = 8
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "7dd4beac2c4c6c595a805576d682d8aa831e6e7d": 131932313,
+    "440a6cd18137860ed1f75428313d5559f2ce01a6": 131987046,
 }
 
 
