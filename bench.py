@@ -41,6 +41,7 @@ BYTES_PER_BLOCK = 512          # 256 B of FP32 coefficients in + 256 B out
 PIXEL_BYTES_PER_BLOCK = 320    # fused pixel output: 256 B of coefficients in + 64 B of uint8 out
 FLOPS_PER_BLOCK_FP32 = 2 * 64 * 64   # one 64 x 64 matrix-vector product
 ROTATE = 8
+GRAPH_STEPS = 200       # steps per captured graph; the timed loop replays several
 
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
@@ -522,14 +523,16 @@ def run_dctf(args):
         torch.cuda.synchronize()
         return g
 
-    def run_timed(g):
+    def run_timed(graphs):
+        graphs = graphs if isinstance(graphs, (list, tuple)) else [graphs]
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.time()
         start.record(stream)
-        g.replay()
+        for g in graphs:
+            g.replay()
         end.record(stream)
         torch.cuda.synchronize()
         t1 = time.time()
@@ -537,15 +540,26 @@ def run_dctf(args):
             dist.barrier()
         return shard.max_over_ranks(start.elapsed_time(end), dist if ws > 1 else None), (t0, t1)
 
+    def chunked(make, steps):
+        """`steps` steps as replays of graphs of at most GRAPH_STEPS steps
+        (one graph of thousands of steps ran ~5% slower per step)."""
+        c = min(steps, GRAPH_STEPS)
+        g = make(c)
+        seq = [g] * (steps // c)
+        if steps % c:
+            seq.append(make(steps % c))
+        return seq
+
     def timed(prec, steps, warmup):
         g_w = loop_graph(max(warmup, 1), prec)
-        g_t = loop_graph(steps, prec)
+        seq = chunked(lambda k: loop_graph(k, prec), steps)
         g_w.replay()
-        total_ms, window = run_timed(g_t)
+        total_ms, window = run_timed(seq)
         # the apply kernel alone, for its roofline: same launches, no builds
-        a_w, a_t = apply_graph(max(warmup, 1), prec), apply_graph(steps, prec)
+        a_w = apply_graph(max(warmup, 1), prec)
+        a_seq = chunked(lambda k: apply_graph(k, prec), steps)
         a_w.replay()
-        apply_ms, _ = run_timed(a_t)
+        apply_ms, _ = run_timed(a_seq)
         return total_ms, apply_ms / steps, window
 
     props = torch.cuda.get_device_properties(dev)
@@ -689,8 +703,9 @@ def run_dctf(args):
         "config": {"workload": WORKLOAD, "blocks_per_step": nb, "precision": "F16X3",
                    "step": "operator rebuild (FP64, 2 kernels) + apply (1 kernel); "
                            "build of step i+1 overlaps apply of step i (three operators)",
-                   "submission": "one CUDA graph per timed loop; applies launched with "
-                                 "DCTF_APPLY_INPUTS_READY (programmatic dependent launch)",
+                   "submission": "CUDA graphs of %d steps replayed back to back (K steps in "
+                                 "all); applies launched with DCTF_APPLY_INPUTS_READY "
+                                 "(programmatic dependent launch)" % GRAPH_STEPS,
                    "build_us": build_us,
                    "l2": f"{ROTATE} rotating input/output buffer pairs, "
                          f"{ROTATE * 2 * nb * 256 / 1e9:.2f} GB > L2",
@@ -700,7 +715,8 @@ def run_dctf(args):
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "apply_group_kernel<float,4,1,false> (one item)",
                      "apply_us_mean": 1e3 * apply_mean,
-                     "timing": "events around K back-to-back applies in one CUDA graph"},
+                     "timing": "events around K back-to-back applies (CUDA graphs of "
+                               "%d applies replayed back to back)" % GRAPH_STEPS},
         "fp32_simt": simt,
         "fused_pixels": fused_pixels,
         "planar_layout": planar,
