@@ -647,7 +647,7 @@ def run_dctf(args):
     del pl_in, pl_out
     op = ops[0]
     op.set_precision(lib.F16X3)
-    # the operator build alone (2 kernels), for the record
+    # the operator build alone (one kernel), for the record
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     b0.record(stream)
     for _ in range(100):
@@ -701,7 +701,7 @@ def run_dctf(args):
         "vs_baseline": None, "dtype": "f32 (f16x3 tensor-core split, fp32 accumulate)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "blocks_per_step": nb, "precision": "F16X3",
-                   "step": "operator rebuild (FP64, 2 kernels) + apply (1 kernel); "
+                   "step": "operator rebuild (FP64, 1 kernel) + apply (1 kernel); "
                            "build of step i+1 overlaps apply of step i (three operators)",
                    "submission": "CUDA graphs of %d steps replayed back to back (K steps in "
                                  "all); applies launched with DCTF_APPLY_INPUTS_READY "

@@ -8,12 +8,15 @@
 // formed: a product with K is the separable 2-D DCT C X C^T of the vector
 // reshaped to N x N, so M costs 4 N^5 multiply-adds instead of 2 N^6.
 //
-// Two launches, both one CTA per row/column of an N^2 x N^2 matrix:
-//   build_hg: row p of H (a1) and row p of G = H K^T (first half of a2);
-//   build_m : column q of M = K G (second half of a2), its FP32 copy and the
-//             low-precision pieces (a3) in the tensor-core B layout: FP16
-//             hi/lo, and for 16x16 blocks also three BF16 pieces and TF32
-//             hi/lo.
+// One launch, one CTA per column q of the N^2 x N^2 operator:
+//   row q of H (a1, kept for download);
+//   column q of G = H K^T: G[p][q] = sum_b H[p][b] K[q][b] is the spatial
+//     filter applied to DCT basis image q, so it comes straight from the mask
+//     taps (first half of a2);
+//   column q of M = K G (second half of a2), its FP32 copy and the
+//     low-precision pieces (a3) in the tensor-core B layout: FP16 hi/lo, and
+//     for 16x16 blocks also three BF16 pieces and TF32 hi/lo; for 8x8 blocks
+//     the FP16 pieces of the pixel operator G.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -64,68 +67,28 @@ __device__ inline void load_c(double (*cs)[kMaxN + 1], const double *__restrict_
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) cs[t / n][t % n] = C[t];
 }
 
-__global__ void build_hg_kernel(const MaskParams mp, const double *__restrict__ C,
-                                double *__restrict__ H, double *__restrict__ G) {
-  __shared__ double cs[kMaxN][kMaxN + 1];
-  __shared__ double hrow[kMaxN2];
-  __shared__ double tmp[kMaxN2];
-  const int n = mp.n, n2 = n * n, p = blockIdx.x, t = threadIdx.x;
-  const int i = p / n, j = p % n;
-  load_c(cs, C, n);
-  if (t < n2) {
-    // Row (i, j) of H: mask entry (r, c) reads pixel (i + r - ar, j + c - ac)
-    // of the same block (Eq. 5 as a correlation); zero padding drops the
-    // pixels outside the block (Sec. II.B), border replication moves them to
-    // the nearest edge pixel, clamping each axis (Sec. II.C, Eq. 13-18).
-    // Thread t owns column t and adds its entries in (r, c) order.
-    double acc = 0.0;
-    for (int r = 0; r < mp.mh; ++r)
-      for (int c = 0; c < mp.mw; ++c) {
-        int s = i + r - mp.ar, u = j + c - mp.ac;
-        if (mp.boundary == DCTF_ZERO) {
-          if (s < 0 || s >= n || u < 0 || u >= n) continue;
-        } else {
-          s = min(max(s, 0), n - 1);
-          u = min(max(u, 0), n - 1);
-        }
-        if (s * n + u == t) acc += mp.w[r * mp.mw + c];
-      }
-    hrow[t] = acc;
-    H[(size_t)p * n2 + t] = acc;
-  }
-  __syncthreads();
-  // G[p][:] = (H K^T)[p][:] = K H[p][:]^T = vec(C mat(H[p][:]) C^T)
-  double g = dct2_vec(hrow, tmp, cs, n, t);
-  if (t < n2) G[(size_t)p * n2 + t] = g;
-}
-
-__global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restrict__ C,
-                               const double *__restrict__ G, double *__restrict__ M64,
-                               float *__restrict__ M32, float *__restrict__ Mdc,
-                               __half *__restrict__ f16, __nv_bfloat16 *__restrict__ bf16,
-                               uint32_t *__restrict__ tf32, __half *__restrict__ f16_pix,
-                               float *__restrict__ Gdc) {
-  __shared__ double cs[kMaxN][kMaxN + 1];
-  __shared__ double gcol[kMaxN2];
-  __shared__ double tmp[kMaxN2];
-  const int n2 = n * n, q = blockIdx.x, t = threadIdx.x;
-  load_c(cs, C, n);
-  if (t < n2) gcol[t] = G[(size_t)t * n2 + q];
-  __syncthreads();
-  // M[:][q] = K G[:][q] = vec(C mat(G[:][q]) C^T)
-  double m = dct2_vec(gcol, tmp, cs, n, t);
-  if (t >= n2) return;
+// Column q, entry t of M (m) and of G (gq): the FP64 and FP32 copies and
+// every low-precision piece, in the layouts the apply kernels read.
+__device__ __forceinline__ void write_pieces(int n, int q, int t, int f16_scale_exp, double m,
+                                             double gq, double *__restrict__ M64,
+                                             float *__restrict__ M32, float *__restrict__ Mdc,
+                                             __half *__restrict__ f16,
+                                             __nv_bfloat16 *__restrict__ bf16,
+                                             uint32_t *__restrict__ tf32,
+                                             __half *__restrict__ f16_pix,
+                                             float *__restrict__ Gdc) {
+  const int n2 = n * n;
   if (f16_pix != nullptr) {
     // the pixel operator G = H K^T (coefficients -> filtered pixels), split
     // like M: G 2^s = hi + lo in FP16 (|G| obeys the same bound as |M|)
-    const double gs = ldexp(gcol[t], f16_scale_exp);
+    const double gs = ldexp(gq, f16_scale_exp);
     const __half hi = __double2half(gs);
     const __half lo = __double2half(gs - (double)__half2float(hi));
     const int chunk = q >> 6, byte = (q & 63) * 2;
     char *base = reinterpret_cast<char *>(f16_pix);
     *reinterpret_cast<__half *>(base + sw128_offset(t, byte, 2 * n2, chunk)) = hi;
     *reinterpret_cast<__half *>(base + sw128_offset(n2 + t, byte, 2 * n2, chunk)) = lo;
-    if (q == 0) Gdc[t] = (float)gcol[t];
+    if (q == 0) Gdc[t] = (float)gq;
   }
   M64[(size_t)t * n2 + q] = m;
   M32[(size_t)t * n2 + q] = (float)m;
@@ -168,6 +131,63 @@ __global__ void build_m_kernel(int n, int f16_scale_exp, const double *__restric
   }
 }
 
+// Fused build: see the file comment.  Thread t < n2 owns entry t of the
+// column (and of H's row q).
+__global__ void build_kernel(const MaskParams mp, int f16_scale_exp, const double *__restrict__ C,
+                             double *__restrict__ H, double *__restrict__ M64,
+                             float *__restrict__ M32, float *__restrict__ Mdc,
+                             __half *__restrict__ f16, __nv_bfloat16 *__restrict__ bf16,
+                             uint32_t *__restrict__ tf32, __half *__restrict__ f16_pix,
+                             float *__restrict__ Gdc) {
+  __shared__ double cs[kMaxN][kMaxN + 1];
+  __shared__ double gcol[kMaxN2];
+  __shared__ double tmp[kMaxN2];
+  const int n = mp.n, n2 = n * n, q = blockIdx.x, t = threadIdx.x;
+  load_c(cs, C, n);
+  __syncthreads();
+  if (t < n2) {
+    // Row q of H (as a1: mask entry (r, c) of output pixel q reads pixel
+    // (qi + r - ar, qj + c - ac) of the block, Eq. 5 as a correlation; zero
+    // padding drops pixels outside the block, replication clamps each axis,
+    // Sec. II.B-C); thread t owns column t.
+    const int qi = q / n, qj = q % n;
+    double h = 0.0;
+    for (int r = 0; r < mp.mh; ++r)
+      for (int c = 0; c < mp.mw; ++c) {
+        int s = qi + r - mp.ar, u = qj + c - mp.ac;
+        if (mp.boundary == DCTF_ZERO) {
+          if (s < 0 || s >= n || u < 0 || u >= n) continue;
+        } else {
+          s = min(max(s, 0), n - 1);
+          u = min(max(u, 0), n - 1);
+        }
+        if (s * n + u == t) h += mp.w[r * mp.mw + c];
+      }
+    H[(size_t)q * n2 + t] = h;
+    // G[t][q]: output pixel t = (i, j) of the filter applied to basis image
+    // q = (fu, fv), whose pixel (a, b) is K[q][(a, b)] = C[fu][a] C[fv][b]
+    const int i = t / n, j = t % n, fu = q / n, fv = q % n;
+    double g = 0.0;
+    for (int r = 0; r < mp.mh; ++r)
+      for (int c = 0; c < mp.mw; ++c) {
+        int s = i + r - mp.ar, u = j + c - mp.ac;
+        if (mp.boundary == DCTF_ZERO) {
+          if (s < 0 || s >= n || u < 0 || u >= n) continue;
+        } else {
+          s = min(max(s, 0), n - 1);
+          u = min(max(u, 0), n - 1);
+        }
+        g += mp.w[r * mp.mw + c] * (cs[fu][s] * cs[fv][u]);
+      }
+    gcol[t] = g;
+  }
+  __syncthreads();
+  // M[:][q] = K G[:][q] = vec(C mat(G[:][q]) C^T)
+  const double m = dct2_vec(gcol, tmp, cs, n, t);
+  if (t >= n2) return;
+  write_pieces(n, q, t, f16_scale_exp, m, gcol[t], M64, M32, Mdc, f16, bf16, tf32, f16_pix, Gdc);
+}
+
 }  // namespace
 
 cudaError_t launch_dct_matrix(dctf_operator *op, cudaStream_t s) {
@@ -177,12 +197,9 @@ cudaError_t launch_dct_matrix(dctf_operator *op, cudaStream_t s) {
 
 cudaError_t launch_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s) {
   const int n2 = op->n2;
-  build_hg_kernel<<<n2, n2, 0, s>>>(mp, op->d_C64, op->d_H64, op->d_G64);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  build_m_kernel<<<n2, n2, 0, s>>>(op->n, op->f16_scale_exp, op->d_C64, op->d_G64, op->d_M64,
-                                   op->d_M32, op->d_Mdc, op->d_f16, op->d_bf16, op->d_tf32,
-                                   op->d_f16_pix, op->d_Gdc);
+  build_kernel<<<n2, n2, 0, s>>>(mp, op->f16_scale_exp, op->d_C64, op->d_H64, op->d_M64, op->d_M32,
+                                 op->d_Mdc, op->d_f16, op->d_bf16, op->d_tf32, op->d_f16_pix,
+                                 op->d_Gdc);
   return cudaGetLastError();
 }
 

@@ -151,12 +151,11 @@ static dctf_status build_operator(const double *mask, int mh, int mw, const int 
   const bool pieces = tc_supported(n, DCTF_F16X3);
   const bool wide = n == 16;                  // BF16 and TF32 pieces too
   const bool pix = n == 8;                    // pixel operator pieces too
-  size_t off = 0, o_C64, o_M64, o_H64, o_G64, o_M32, o_Mdc, o_f16 = 0, o_bf16 = 0, o_tf32 = 0,
+  size_t off = 0, o_C64, o_M64, o_H64, o_M32, o_Mdc, o_f16 = 0, o_bf16 = 0, o_tf32 = 0,
          o_pix = 0, o_gdc = 0, o_kA = 0, o_kB = 0, o_err;
   o_C64 = off; off = align_up(off + n2 * 8, 1024);
   o_M64 = off; off = align_up(off + sq * 8, 1024);
   o_H64 = off; off = align_up(off + sq * 8, 1024);
-  o_G64 = off; off = align_up(off + sq * 8, 1024);
   o_M32 = off; off = align_up(off + sq * 4, 1024);
   o_Mdc = off; off = align_up(off + n2 * 4, 1024);
   if (pieces) { o_f16 = off; off = align_up(off + 2 * sq * 2, 1024); }
@@ -180,7 +179,6 @@ static dctf_status build_operator(const double *mask, int mh, int mw, const int 
   op->d_C64 = reinterpret_cast<double *>(b + o_C64);
   op->d_M64 = reinterpret_cast<double *>(b + o_M64);
   op->d_H64 = reinterpret_cast<double *>(b + o_H64);
-  op->d_G64 = reinterpret_cast<double *>(b + o_G64);
   op->d_M32 = reinterpret_cast<float *>(b + o_M32);
   op->d_Mdc = reinterpret_cast<float *>(b + o_Mdc);
   op->d_f16 = pieces ? reinterpret_cast<__half *>(b + o_f16) : nullptr;

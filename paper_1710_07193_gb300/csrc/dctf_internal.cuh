@@ -62,7 +62,6 @@ struct dctf_operator {
   double *d_C64;            // [n][n] DCT matrix C (Eq. 1-2), made once at creation
   double *d_M64;            // [n2][n2] FP64 operator, row = output coefficient
   double *d_H64;            // [n2][n2] spatial operator
-  double *d_G64;            // [n2][n2] scratch: H K^T
   float *d_M32;             // [n2][n2] FP32 copy of M
   float *d_Mdc;             // [n2] M[:, 0] in FP32
   __half *d_f16;            // F16X3 pieces: rows 0..n2-1 hi, n2..2n2-1 lo (sw128)
