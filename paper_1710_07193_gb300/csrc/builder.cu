@@ -211,9 +211,11 @@ cudaError_t launch_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s
 // For callers that may not allocate device memory: code running inside a
 // framework that owns every byte of the GPU through its own pool, real-time
 // paths where cudaMalloc's implicit device synchronisation is not allowed,
-// or plug-ins handed only the buffers they read and write.  The build's one
-// scratch buffer (G = H K^T, and H when the caller does not want it) lives in
-// this file-scope array instead of an allocation.  It is 1 MiB, sized for the
+// or plug-ins handed only the buffers they read and write.  It runs the
+// build in its two-pass form, which needs scratch: rows of H and of
+// G = H K^T, then columns of M = K G read back from G.  That scratch (G, and
+// H when the caller does not want it) lives in this file-scope array instead
+// of an allocation.  It is 1 MiB, sized for the
 // largest block (n = 16: two 256 x 256 FP64 matrices), and every GPU that
 // loads the library holds it until the process exits.
 static __device__ __align__(256) double dctf_build_scratch[2 * dctf::kMaxN2 * dctf::kMaxN2];
@@ -223,7 +225,8 @@ namespace {
 
 constexpr size_t kScratchDoubles = 2 * (size_t)kMaxN2 * kMaxN2;
 
-// Same arithmetic as build_hg_kernel; H is optional here.
+// Pass 1: row p of H (mask entries added in (r, c) order, as in build_kernel,
+// so H is bit-identical) and row p of G = H K^T = vec(C mat(H[p]) C^T).
 __global__ void build_hg_noalloc_kernel(const MaskParams mp, double *__restrict__ H,
                                         double *__restrict__ G) {
   __shared__ double cs[kMaxN][kMaxN + 1];
@@ -253,7 +256,7 @@ __global__ void build_hg_noalloc_kernel(const MaskParams mp, double *__restrict_
   if (t < n2) G[(size_t)p * n2 + t] = g;
 }
 
-// Same arithmetic as build_m_kernel; writes M (FP64) only.
+// Pass 2: column q of M = K G (FP64 only).
 __global__ void build_m_noalloc_kernel(int n, const double *__restrict__ G,
                                        double *__restrict__ M64) {
   __shared__ double cs[kMaxN][kMaxN + 1];
