@@ -710,7 +710,7 @@ def run_dctf(args):
                    "l2": f"{ROTATE} rotating input/output buffer pairs, "
                          f"{ROTATE * 2 * nb * 256 / 1e9:.2f} GB > L2",
                    "parallelism": f"dp{ws} (independent images, no collective)"},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 2 * args.steps,     # per step: build_kernel + apply_group_kernel
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "apply_group_kernel<float,4,1,false> (one item)",
