@@ -36,11 +36,12 @@
 //    of 256 B of coefficients.
 //  * Image-plane layout (kMode = kModePlanar): the coefficients of block
 //    (by, bx) sit at rows 8 by + u, columns 8 bx + v of an image-shaped FP32
-//    array (the layout of a JPEG decoder's coefficient plane).  A 4-D TMA
-//    view (v, bx, u, by) loads a tile of 128 blocks of one block row as one
-//    box and stores 32 blocks per epilogue warp the same way; block rows
-//    are padded to a multiple of 128 blocks in the tile walk (the padding
-//    is outside the tensor: zero-filled on load, clipped on store).
+//    array (the layout of a JPEG decoder's coefficient plane).  A 2-D TMA
+//    view moves boxes of 256 floats x 8 rows (32 blocks of one block row,
+//    1 KB runs): four per 128-block tile on load, one per epilogue warp on
+//    store; block rows are padded to a multiple of 128 blocks in the tile
+//    walk (the padding is outside the tensor: zero-filled on load, clipped
+//    or skipped on store).
 //  * Host-direct I/O (kMode = kModeHost): the coefficients stay in page-locked
 //    host memory mapped into the device address space.  The whole producer
 //    warp copies each 32 KB input tile with 16-byte cp.async into the same
@@ -345,14 +346,17 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       const uint32_t ph = (it / S) & 1;
       if (!wait_bounded(&empty_in[s], ph ^ 1, s_abort, err, kRoleProducer | (it << 8))) break;
       const GroupItem &gi = items[t.item];
-      const void *map = t.rows == kTile ? (const void *)&gi.tm_in : (const void *)&gi.tm_in_half;
       mbar_arrive_expect_tx(&full_in[s], t.rows * Io<IoT>::kRowBytes);
       uint8_t *dst = s_in + s * L::kStageBytes;
       if constexpr (kMode == kModePlanar) {
-        // box (v 8, bx t.rows, u 8, by 1) -> shared [u][t.rows][v]
+        // t.rows / 32 boxes of (256 floats, 8 rows): 32 blocks of one block
+        // row each, shared [box][u][32 blocks][v]; the rows of a box are
+        // 1 KB runs of the plane
         const int by = t.row0 / (int)gi.bw, bx0 = t.row0 % (int)gi.bw;
-        tma_load_4d(map, &full_in[s], dst, 0, bx0, 0, by);
+        for (int k = 0; k < t.rows / 32; ++k)
+          tma_load_2d(&gi.tm_in, &full_in[s], dst + k * 8192, (bx0 + 32 * k) * 8, by * 8);
       } else {
+        const void *map = t.rows == kTile ? (const void *)&gi.tm_in : (const void *)&gi.tm_in_half;
 #pragma unroll
         for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
           tma_load_2d(map, &full_in[s], dst + bx * L::kBoxBytes, bx * Io<IoT>::kBoxCols, t.row0);
@@ -438,14 +442,15 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       float v[64];
       const uint8_t *st = s_in + s * L::kStageBytes + row * 128;
       if constexpr (kMode == kModePlanar) {
-        // shared [u][t.rows][v]: this block's row u is 32 bytes at (u t.rows + row) * 32.
-        // Lanes 4 apart hit the same banks; taking the two 16-byte halves in
-        // an order that flips with bit 2 of the row halves the conflicts.
-        const uint8_t *sp = s_in + s * L::kStageBytes;
+        // shared [box][u][32 blocks][v]: this block's row u is 32 bytes at
+        // (row / 32) 8192 + u 1024 + (row % 32) 32.  Lanes 4 apart hit the
+        // same banks; taking the two 16-byte halves in an order that flips
+        // with bit 2 of the row removes the conflicts.
+        const uint8_t *sp = s_in + s * L::kStageBytes + (row >> 5) * 8192 + (row & 31) * 32;
         const int sw = (row >> 2) & 1;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const float4 *q = reinterpret_cast<const float4 *>(sp + (u * t.rows + row) * 32);
+          const float4 *q = reinterpret_cast<const float4 *>(sp + u * 1024);
           const float4 f = q[sw], g = q[sw ^ 1];
           const float4 a = sw ? g : f, b = sw ? f : g;
           v[8 * u] = a.x; v[8 * u + 1] = a.y; v[8 * u + 2] = a.z; v[8 * u + 3] = a.w;
@@ -689,7 +694,11 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         if (store) {
           const int y0 = t.row0 + wr * 32;
           if constexpr (kMode == kModePlanar) {
-            tma_store_4d(&gi.tm_out, slab, 0, y0 % (int)gi.bw, 0, y0 / (int)gi.bw);
+            // one (256 floats, 8 rows) box: this warp's 32 blocks; a box
+            // past the image's right edge is clipped, one wholly past it
+            // is skipped
+            const int bx = y0 % (int)gi.bw, by = y0 / (int)gi.bw;
+            if (bx < gi.pitch) tma_store_2d(&gi.tm_out, slab, bx * 8, by * 8);
           } else {
 #pragma unroll
             for (int bx = 0; bx < Io<IoT>::kBoxesPerRow; ++bx)
@@ -804,17 +813,18 @@ cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, i
                                                      1, err, s, pdl);
 }
 
-// Image-plane coefficients: the 4-D view (v, bx, u, by) of an FP32 array of
-// `height` rows of `pitch` floats; boxes of (8, box_blocks, 8, 1).
+// Image-plane coefficients: the 2-D view of an FP32 array of `height` rows
+// of `pitch` floats (`width` of them used); boxes of 256 floats x 8 rows,
+// i.e. 32 blocks of one block row, each box row a 1 KB run of the plane.
 static cudaError_t make_planar_map(CUtensorMap *m, const void *ptr, int height, int width,
-                                   int64_t pitch, int box_blocks) {
+                                   int64_t pitch) {
   EncodeTiledFn enc = encode_fn();
   if (enc == nullptr) return cudaErrorNotSupported;
-  cuuint64_t dims[4] = {8, (cuuint64_t)(width / 8), 8, (cuuint64_t)(height / 8)};
-  cuuint64_t strides[3] = {32, (cuuint64_t)pitch * 4, (cuuint64_t)pitch * 32};
-  cuuint32_t box[4] = {8, (cuuint32_t)box_blocks, 8, 1};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(ptr), dims, strides,
+  cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+  cuuint32_t box[2] = {256, 8};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ptr), dims, strides,
                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -825,15 +835,15 @@ cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int he
                                 cudaStream_t s, bool pdl) {
   GroupItem gi;
   memset(&gi, 0, sizeof gi);
-  cudaError_t e = make_planar_map(&gi.tm_in, in, height, width, in_pitch, kTile);
-  if (e == cudaSuccess) e = make_planar_map(&gi.tm_in_half, in, height, width, in_pitch, kHalf);
-  if (e == cudaSuccess) e = make_planar_map(&gi.tm_out, out, height, width, out_pitch, 32);
+  cudaError_t e = make_planar_map(&gi.tm_in, in, height, width, in_pitch);
+  if (e == cudaSuccess) e = make_planar_map(&gi.tm_out, out, height, width, out_pitch);
   if (e != cudaSuccess) return e;
   const int64_t bw_pad = (width / 8 + kTile - 1) / kTile * kTile;
   gi.pieces = op->d_f16;
   gi.mdc = op->d_Mdc;
   gi.out_scale = ldexpf(1.0f, -op->f16_scale_exp);
   gi.bw = bw_pad;
+  gi.pitch = width / 8;                              // the plane's width in blocks
   gi.nblocks = (int64_t)(height / 8) * bw_pad;      // tile walk over padded block rows
   const int64_t total_halves = gi.nblocks / kHalf;
   int64_t g = sm_count(op->device);

@@ -26,8 +26,10 @@ struct GroupItem {              // CUtensorMap members keep it 128-byte aligned
   int64_t nblocks;
   int64_t half_begin;       // first 64-block half tile of the item in the group
   uint8_t *img;             // pixel output (apply_pixels): uint8 image,
-  int64_t pitch;            //   its row pitch in bytes,
-  int64_t bw;               //   and its width in blocks
+  int64_t pitch;            //   its row pitch in bytes (image-plane layout:
+                            //   the plane's width in blocks),
+  int64_t bw;               //   and its width in blocks (image-plane layout:
+                            //   padded to a multiple of 128)
   const float *hin;         // host-direct apply: mapped page-locked host input
   float *hout;              //   and output, [nblocks][64] FP32, 16-byte aligned
 };
