@@ -46,7 +46,7 @@ GRAPH_STEPS = 200       # steps per captured graph; the timed loop replays sever
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "440a6cd18137860ed1f75428313d5559f2ce01a6": 131987046,
+    "8c07e3c08c7f8f4fae9eed90ef5489a84e06a306": 131883366,
 }
 
 
