@@ -217,7 +217,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ serving
-SERVING_RATES = (1000.0, 2000.0, 5000.0, 10000.0, 20000.0, 40000.0)
+SERVING_RATES = (1000.0, 2000.0, 5000.0, 10000.0, 15000.0, 20000.0, 30000.0, 40000.0)
 
 
 def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
