@@ -251,7 +251,9 @@ def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
 
     def serve(n, rate):
         stream = datagen.serving_stream(n, rate, with_pixels=False)
-        srv = lib.Server(hbm_budget_bytes=1 << 30, max_inflight=3, max_batch_requests=16,
+        # eight batches in flight: the copy in, apply and copy out of a batch
+        # are ordered on its stream, so more batches overlap on the link
+        srv = lib.Server(hbm_budget_bytes=2 << 30, max_inflight=8, max_batch_requests=16,
                          op_cache_capacity=64)
         # every request is marshalled before the stream starts, so the
         # submitter only waits for arrival times and makes one native call
