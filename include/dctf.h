@@ -341,7 +341,8 @@ dctf_status dctf_group_create_pixels(const dctf_pixel_item *items, int nitems,
  * requests in arrival order while a batch slot is free and their device
  * memory fits in the HBM budget, reuses or builds their operators (device
  * cache keyed by mask, anchor and boundary; FP64 build), and runs each batch
- * as one grouped launch with dequantise / requantise fused; up to
+ * as grouped launches with dequantise / requantise fused (one for the planes
+ * it reads and writes in host memory itself, one for planes staged in HBM); up to
  * max_inflight batches overlap on the device.  Results do not depend on the
  * batch a request lands in. */
 typedef struct {
@@ -370,6 +371,7 @@ typedef struct {
     uint64_t completed, failed, batches, blocks, cache_hits, cache_misses;
     int max_batch_requests_seen;
     size_t hbm_in_use;
+    uint64_t direct_requests;                /* completed on the host-direct route */
 } dctf_stats;
 
 typedef struct dctf_server dctf_server;
@@ -379,9 +381,16 @@ typedef struct dctf_server dctf_server;
 dctf_status dctf_server_create(const dctf_server_cfg *cfg, dctf_server **out);
 
 /* Queue a request; its host buffers must stay valid until dctf_server_wait
- * returns for its ticket.  Page-locked buffers (cudaHostAlloc or
- * cudaHostRegister) are copied by DMA directly; others go through the
- * server's pinned staging.  EBUDGET if it can never fit the HBM budget. */
+ * returns for its ticket.  Routes, chosen per request at submit:
+ *  - host-direct: every plane's input and output is page-locked, mapped
+ *    memory (cudaHostAlloc, cudaHostRegister), 16-byte aligned, and no two
+ *    of the request's buffers overlap except a plane filtered in place
+ *    (in == out).  The batch kernel reads and writes these planes over the
+ *    host link itself; the request takes no HBM from the budget.
+ *  - staged: otherwise.  Page-locked buffers are copied by DMA directly,
+ *    others go through the server's pinned staging; EBUDGET if the planes
+ *    can never fit the HBM budget.
+ * Both routes give the same bits. */
 dctf_status dctf_server_submit(dctf_server *s, const dctf_request *req,
                                uint64_t *ticket);
 

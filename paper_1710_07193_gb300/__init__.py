@@ -364,7 +364,7 @@ class _Stats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("blocks", ctypes.c_uint64), ("cache_hits", ctypes.c_uint64),
                 ("cache_misses", ctypes.c_uint64), ("max_batch_requests_seen", _i32),
-                ("hbm_in_use", ctypes.c_size_t)]
+                ("hbm_in_use", ctypes.c_size_t), ("direct_requests", ctypes.c_uint64)]
 
 
 _SIGS.update({

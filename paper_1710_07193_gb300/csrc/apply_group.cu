@@ -309,10 +309,12 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
 
   if (kMode == kModeHost && warp == 0) {
     // ---------------------------------------------------------- host producer
-    // The tile's rows are contiguous: chunk c (16 bytes) of the tile is
-    // coefficients 4 (c % 16) .. +3 of row c / 16, and lane l copies chunks
-    // l, l + 32, ...  (a warp reads 512 contiguous bytes per step).  Each
-    // chunk lands where the 128-byte-swizzled TMA box would put it.
+    // The tile's rows are contiguous: chunk c (16 bytes) of the tile is chunk
+    // c % kCPR of row c / kCPR (kCPR = 16 for FP32 rows, 8 for int16), and
+    // lane l copies chunks l, l + 32, ...  (a warp reads 512 contiguous bytes
+    // per step).  Each chunk lands where the 128-byte-swizzled TMA box would
+    // put it.
+    constexpr int kCPR = Io<IoT>::kRowBytes / 16;
     int it = 0;
     while (walk.next(t)) {
       const int s = it % S;
@@ -321,12 +323,12 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       const GroupItem &gi = items[t.item];
       const int64_t left = gi.nblocks - t.row0;
       const int valid = left < t.rows ? (int)left : t.rows;     // rows past the end: zeros
-      const float4 *src = reinterpret_cast<const float4 *>(gi.hin) + (int64_t)t.row0 * 16;
+      const uint4 *src = reinterpret_cast<const uint4 *>(gi.hin) + (int64_t)t.row0 * kCPR;
       const uint32_t dst = smem_u32(s_in + s * L::kStageBytes);
-      const int nchunks = t.rows * 16;
+      const int nchunks = t.rows * kCPR;
 #pragma unroll 8
       for (int c = lane; c < nchunks; c += 32) {
-        const int r = c >> 4, u = c & 15;
+        const int r = c / kCPR, u = c % kCPR;
         const uint32_t d = dst + (u >> 3) * L::kBoxBytes + r * 128 + (((u & 7) ^ (r & 7)) << 4);
         const bool ok = r < valid;
         cp_async_16(d, ok ? src + c : src, ok ? 16u : 0u);
@@ -618,34 +620,9 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       }
       const bool store = wr * 32 < t.rows;
       uint8_t *slab = s_out + o * L::kStageBytes + wr * L::kSlabBytes;
-      if constexpr (kMode == kModeHost) {
-        // stage this warp's 32 rows (swizzled as for the TMA store), then
-        // copy them out: chunk c = lane + 32 i is 16 bytes of row c / 16, so
-        // a warp writes 512 contiguous bytes per step.  Slab o was last read
-        // two tiles ago, before the __syncwarp of the previous tile.
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-          *reinterpret_cast<float4 *>(slab + (u >> 3) * L::kSlabBoxBytes + r32 * 128 +
-                                      (((u & 7) ^ (r32 & 7)) << 4)) =
-              make_float4(acc[4 * u], acc[4 * u + 1], acc[4 * u + 2], acc[4 * u + 3]);
-        __syncwarp();
-        if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's M[:,0]
-        const int64_t y0 = (int64_t)t.row0 + wr * 32;
-        const int64_t left = gi.nblocks - y0;
-        const int lim = t.rows - wr * 32 < 32 ? t.rows - wr * 32 : 32;
-        const int nrows = (int)(left < lim ? left : lim);     // <= 0: nothing to store
-        float4 *dst = reinterpret_cast<float4 *>(gi.hout) + y0 * 16;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int c = lane + 32 * i, r = c >> 4, u = c & 15;
-          if (r < nrows)
-            __stcs(dst + c, *reinterpret_cast<const float4 *>(
-                                slab + (u >> 3) * L::kSlabBoxBytes + r * 128 + (((u & 7) ^ (r & 7)) << 4)));
-        }
-        ++it;
-        continue;
-      }
-      if (lane == 0) bulk_wait_read<1>();             // slab o free (store of tile it-2 read it)
+      // slab o is free: the TMA store of tile it - 2 has read it (host mode:
+      // the lanes' copies of tile it - 2 came before the previous __syncwarp)
+      if (kMode != kModeHost && lane == 0) bulk_wait_read<1>();
       __syncwarp();
       if constexpr (kMode == kModePlanar) {
         // shared [u][32][v] for this warp's 32 blocks (halves in the
@@ -690,6 +667,26 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       fence_async_smem();
       __syncwarp();
       if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's M[:,0], q_out
+      if constexpr (kMode == kModeHost) {
+        // copy the staged rows to host memory: chunk c = lane + 32 i is chunk
+        // c % kCPR of row c / kCPR, so a warp writes 512 contiguous bytes per
+        // step
+        constexpr int kCPR = Io<IoT>::kRowBytes / 16;
+        const int64_t y0 = (int64_t)t.row0 + wr * 32;
+        const int64_t left = gi.nblocks - y0;
+        const int lim = t.rows - wr * 32 < 32 ? t.rows - wr * 32 : 32;
+        const int nrows = (int)(left < lim ? left : lim);     // <= 0: nothing to store
+        uint4 *dst = reinterpret_cast<uint4 *>(gi.hout) + y0 * kCPR;
+#pragma unroll
+        for (int i = 0; i < kCPR; ++i) {
+          const int c = lane + 32 * i, r = c / kCPR, u = c % kCPR;
+          if (r < nrows)
+            __stcs(dst + c, *reinterpret_cast<const uint4 *>(
+                                slab + (u >> 3) * L::kSlabBoxBytes + r * 128 + (((u & 7) ^ (r & 7)) << 4)));
+        }
+        ++it;
+        continue;
+      }
       if (lane == 0) {
         if (store) {
           const int y0 = t.row0 + wr * 32;
@@ -802,6 +799,23 @@ cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *
   return cudaSuccess;
 }
 
+cudaError_t fill_group_item_host(GroupItem *gi, const dctf_operator *op, const void *hin,
+                                 void *hout, int64_t nblocks, const uint16_t *qin,
+                                 const uint16_t *qout) {
+  memset(gi, 0, sizeof *gi);
+  if (((reinterpret_cast<uintptr_t>(hin) | reinterpret_cast<uintptr_t>(hout)) & 15) != 0)
+    return cudaErrorInvalidValue;
+  gi->pieces = op->d_f16;
+  gi->mdc = op->d_Mdc;
+  gi->qin = qin;
+  gi->qout = qout;
+  gi->out_scale = ldexpf(1.0f, -op->f16_scale_exp);
+  gi->nblocks = nblocks;
+  gi->hin = hin;
+  gi->hout = hout;
+  return cudaSuccess;
+}
+
 cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, int grid,
                                 uint32_t *err, cudaStream_t s, bool pdl) {
   if (total_halves <= 0) return cudaSuccess;
@@ -874,6 +888,20 @@ cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halv
   // host memory in flight stays one compact window
   return launch_cfg<float, 4, 1, false, kModeHost>(nullptr, single, 1, total_halves, (int)g, 1, 1,
                                                    err, s, false);
+}
+
+cudaError_t launch_apply_group_host(const GroupItem *d_items, int nitems, int64_t total_halves,
+                                    int grid, uint32_t *err, cudaStream_t s) {
+  if (total_halves <= 0) return cudaSuccess;
+  int64_t g = grid > 0 ? grid : 0;
+  if (g > total_halves) g = total_halves;
+  if (g < 1) g = 1;
+  static const GroupItem kEmpty = {};
+  // 128-row tiles: each stage holds a whole tile, so twice the host reads
+  // are in flight per CTA as with 64-row tiles (serving stream: 42k req/s
+  // sustained against 23-25k with 64-row tiles)
+  return launch_cfg<int16_t, 4, 2, true, kModeHost>(d_items, kEmpty, nitems, total_halves, (int)g, 2,
+                                                    0, err, s, false);
 }
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,

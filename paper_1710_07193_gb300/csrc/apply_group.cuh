@@ -30,13 +30,18 @@ struct GroupItem {              // CUtensorMap members keep it 128-byte aligned
                             //   the plane's width in blocks),
   int64_t bw;               //   and its width in blocks (image-plane layout:
                             //   padded to a multiple of 128)
-  const float *hin;         // host-direct apply: mapped page-locked host input
-  float *hout;              //   and output, [nblocks][64] FP32, 16-byte aligned
+  const void *hin;          // host-direct apply: mapped page-locked host input
+  void *hout;               //   and output, [nblocks][64] FP32 or int16, 16-byte aligned
 };
 
 cudaError_t fill_group_item(GroupItem *gi, const dctf_operator *op, const void *in, void *out,
                             int64_t nblocks, bool i16, const uint16_t *qin,
                             const uint16_t *qout);
+// Descriptor of a host-direct item: hin / hout are device addresses of
+// mapped page-locked host memory (16-byte aligned); no tensor maps.
+cudaError_t fill_group_item_host(GroupItem *gi, const dctf_operator *op, const void *hin,
+                                 void *hout, int64_t nblocks, const uint16_t *qin,
+                                 const uint16_t *qout);
 
 // d_items: device array (group mode, single == nullptr) or single: one item
 // passed by value.  grid <= 0 means one CTA per SM.  max_take: 2 for 128-row
@@ -70,6 +75,12 @@ cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halv
 // schedule, two operator slots.
 cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int64_t total_halves,
                                       int grid, int max_take, uint32_t *err, cudaStream_t s);
+
+// Host-direct grouped apply of int16 items (serving): each item's hin/hout
+// are mapped page-locked host buffers, its quantisation tables and operator
+// pieces are in device memory; 128-block tiles, contiguous schedule.
+cudaError_t launch_apply_group_host(const GroupItem *d_items, int nitems, int64_t total_halves,
+                                    int grid, uint32_t *err, cudaStream_t s);
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,

@@ -68,7 +68,7 @@ static PointerAttrFn pointer_attr_fn() {
 // over a narrower window of host memory move faster.
 constexpr int kHostDirectCtas = 32;
 
-static void *mapped_host(const void *p, size_t bytes) {
+void *mapped_host(const void *p, size_t bytes) {
   if (p == nullptr) return nullptr;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {

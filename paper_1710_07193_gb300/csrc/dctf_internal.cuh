@@ -113,4 +113,9 @@ cudaError_t launch_apply_kron(const dctf_operator *op, const float *x, int64_t n
 
 int sm_count(int device);
 
+// Host memory a kernel can read and write directly: page-locked, mapped into
+// the device address space, [p, p + bytes) inside one allocation.  Returns
+// the device address of p, or nullptr.
+void *mapped_host(const void *p, size_t bytes);
+
 }  // namespace dctf

@@ -9,11 +9,14 @@
 //   * builds or reuses each request's operator: an LRU cache keyed by
 //     (mask, anchor, boundary, n), FP64 build on its own stream, an event
 //     marks it ready; operators used by an in-flight batch are never evicted;
-//   * launches the batch: host -> HBM copies (straight from the caller's
-//     buffers when they are page-locked, else through pinned staging), ONE
-//     persistent grouped kernel over all planes of all admitted requests
-//     (dequantise, filter, requantise fused), HBM -> host copies, all on the
-//     slot's stream.
+//   * launches the batch on the slot's stream: one upload of the batch's
+//     descriptors, quantisation tables and zeroed status word; for requests
+//     whose planes are mapped page-locked memory, ONE host-direct grouped
+//     kernel that reads and writes those planes over the host link itself
+//     (no copies, no device memory); for the others, host -> HBM copies
+//     (straight from page-locked buffers, else through pinned staging), ONE
+//     persistent grouped kernel over their planes and HBM -> host copies.
+//     Both kernels dequantise, filter and requantise in one pass.
 // Several slots are in flight at once on separate streams, so requests that
 // arrive while a batch runs are admitted as soon as a slot and memory free
 // up, and their copies and kernels overlap the running batch on the device.
@@ -39,6 +42,11 @@ namespace {
 
 constexpr int kMaxPlanes = 4;
 constexpr size_t kAlign = 256;
+constexpr int kQBytes = 128;        // one quantisation table
+// CTAs of a host-direct batch.  The host link bounds it; on the serving
+// stream 64 CTAs sustained the most (42.4k req/s; 16: 37.6k, 32: 40.4k,
+// 152: 42.3k with a longer tail), leaving SMs to the other batches in flight.
+constexpr int kDirectCtas = 64;
 
 double now_ms() {
   using namespace std::chrono;
@@ -129,14 +137,18 @@ struct Req {
   uint16_t q[kMaxPlanes][64] = {};
   OpKey key;
   double t_submit = 0, t_done = 0;
-  // arena layout: [inputs][q tables][outputs], each plane 256-aligned
+  // arena layout: [inputs][outputs], each plane 256-aligned (host-direct
+  // requests take no device memory: bytes = 0)
   size_t off = 0, bytes = 0, in_bytes = 0, out_start = 0;
-  size_t in_off[kMaxPlanes] = {}, q_off[kMaxPlanes] = {}, out_off[kMaxPlanes] = {};
+  size_t in_off[kMaxPlanes] = {}, out_off[kMaxPlanes] = {};
+  const void *din[kMaxPlanes] = {};   // host-direct: device addresses of the planes
+  void *dout[kMaxPlanes] = {};
   OpEntry *op = nullptr;
   dctf_status status = DCTF_OK;
   bool done = false;
   bool in_pinned = false;    // caller buffers already page-locked: copied by DMA directly
   bool out_pinned = false;
+  bool direct = false;       // every plane mapped page-locked: the kernel does the I/O
 };
 
 // Page-locked (or registered) host memory can be the source / target of an
@@ -150,12 +162,42 @@ bool is_pinned(const void *p) {
   return a.type == cudaMemoryTypeHost;
 }
 
+// Host-direct eligibility: every plane's input and output 16-byte aligned
+// and mapped, and no two of the request's buffers overlapping unless a plane
+// is filtered in place (in == out).  Fills the device addresses.
+bool direct_planes(Req *r) {
+  for (int p = 0; p < r->nplanes; ++p) {
+    const size_t len = (size_t)r->nblocks[p] * 128;
+    if ((reinterpret_cast<uintptr_t>(r->in[p]) | reinterpret_cast<uintptr_t>(r->out[p])) & 15)
+      return false;
+    r->din[p] = mapped_host(r->in[p], len);
+    r->dout[p] = mapped_host(r->out[p], len);
+    if (r->din[p] == nullptr || r->dout[p] == nullptr) return false;
+  }
+  auto overlap = [](const void *a, size_t la, const void *b, size_t lb) {
+    const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+    return x < y + lb && y < x + la;
+  };
+  for (int p = 0; p < r->nplanes; ++p) {
+    const size_t lp = (size_t)r->nblocks[p] * 128;
+    if (r->in[p] != r->out[p] && overlap(r->in[p], lp, r->out[p], lp)) return false;
+    for (int q = p + 1; q < r->nplanes; ++q) {
+      const size_t lq = (size_t)r->nblocks[q] * 128;
+      if (overlap(r->in[p], lp, r->in[q], lq) || overlap(r->in[p], lp, r->out[q], lq) ||
+          overlap(r->out[p], lp, r->in[q], lq) || overlap(r->out[p], lp, r->out[q], lq))
+        return false;
+    }
+  }
+  return true;
+}
+
+// Per-batch upload buffer (pinned on the host, mirrored on the device):
+// [GroupItem x nitems][q table x nitems][status word], packed per batch.
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   GroupItem *h_items = nullptr;   // pinned
   GroupItem *d_items = nullptr;
-  uint32_t *d_err = nullptr;
   uint32_t *h_err = nullptr;      // pinned copy of the status word
   int cap = 0;
   bool busy = false;
@@ -186,6 +228,7 @@ struct dctf_server {
   // statistics (under mu)
   std::vector<double> lat_ms;
   uint64_t completed = 0, failed = 0, batches = 0, blocks = 0, hits = 0, misses = 0, builds = 0;
+  uint64_t direct = 0;
   double t_first_submit = 0, t_last_done = 0;
   int max_batch_seen = 0;
 };
@@ -256,6 +299,7 @@ void finish(dctf_server *s, Req *r, dctf_status st) {
   if (st == DCTF_OK) {
     s->lat_ms.push_back(r->t_done - r->t_submit);
     ++s->completed;
+    if (r->direct) ++s->direct;
     for (int p = 0; p < r->nplanes; ++p) s->blocks += r->nblocks[p];
   } else {
     ++s->failed;
@@ -276,7 +320,7 @@ void retire(dctf_server *s) {
       }
       if (r->op) --r->op->refs;
       std::lock_guard<std::mutex> lk(s->mu);
-      s->arena.release(r->off, r->bytes);
+      if (r->bytes > 0) s->arena.release(r->off, r->bytes);
       finish(s, r, r->status != DCTF_OK ? r->status : kst);
     }
     sl.reqs.clear();
@@ -286,49 +330,66 @@ void retire(dctf_server *s) {
 }
 
 dctf_status launch_batch(dctf_server *s, Slot &sl, std::vector<Req *> &batch) {
-  int nitems = 0;
-  int64_t halves = 0;
+  // descriptors: host-direct planes first, then staged planes; each group's
+  // half_begin counts from its own start
+  int nitems = 0, ndirect = 0;
   for (Req *r : batch) {
     r->status = get_op(s, r);
+    if (r->status == DCTF_OK && r->direct) ndirect += r->nplanes;
+    if (r->status == DCTF_OK) nitems += r->nplanes;
+  }
+  char *hb = reinterpret_cast<char *>(sl.h_items), *db = reinterpret_cast<char *>(sl.d_items);
+  const size_t q0 = (size_t)nitems * sizeof(GroupItem);
+  const size_t err_off = q0 + (size_t)nitems * kQBytes;
+  uint32_t *d_err = reinterpret_cast<uint32_t *>(db + err_off);
+  int id = 0, is = ndirect;
+  int64_t hd = 0, hs = 0;
+  cudaError_t e = cudaSuccess;
+  for (Req *r : batch) {
     if (r->status != DCTF_OK) continue;
-    cudaError_t e = cudaSuccess;
-    for (int p = 0; p < r->nplanes; ++p) memcpy(s->h_arena + r->q_off[p], r->q[p], 128);
-    if (r->in_pinned) {
-      for (int p = 0; p < r->nplanes && e == cudaSuccess; ++p)
-        e = cudaMemcpyAsync(s->d_arena + r->in_off[p], r->in[p], (size_t)r->nblocks[p] * 128,
+    if (!r->direct) {
+      if (r->in_pinned) {
+        for (int p = 0; p < r->nplanes && e == cudaSuccess; ++p)
+          e = cudaMemcpyAsync(s->d_arena + r->in_off[p], r->in[p], (size_t)r->nblocks[p] * 128,
+                              cudaMemcpyHostToDevice, sl.stream);
+      } else {
+        for (int p = 0; p < r->nplanes; ++p)
+          memcpy(s->h_arena + r->in_off[p], r->in[p], (size_t)r->nblocks[p] * 128);
+        e = cudaMemcpyAsync(s->d_arena + r->off, s->h_arena + r->off, r->in_bytes,
                             cudaMemcpyHostToDevice, sl.stream);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_arena + r->q_off[0], s->h_arena + r->q_off[0],
-                            (size_t)r->nplanes * kAlign, cudaMemcpyHostToDevice, sl.stream);
-    } else {
-      for (int p = 0; p < r->nplanes; ++p)
-        memcpy(s->h_arena + r->in_off[p], r->in[p], (size_t)r->nblocks[p] * 128);
-      e = cudaMemcpyAsync(s->d_arena + r->off, s->h_arena + r->off, r->in_bytes,
-                          cudaMemcpyHostToDevice, sl.stream);
+      }
     }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.stream, r->op->ready, 0);
     if (e != cudaSuccess) return cuda_error(e, "batch input copy");
     for (int p = 0; p < r->nplanes; ++p) {
-      GroupItem &gi = sl.h_items[nitems++];
-      e = fill_group_item(&gi, r->op->op, s->d_arena + r->in_off[p], s->d_arena + r->out_off[p],
-                          r->nblocks[p], true,
-                          reinterpret_cast<const uint16_t *>(s->d_arena + r->q_off[p]),
-                          reinterpret_cast<const uint16_t *>(s->d_arena + r->q_off[p]));
-      if (e != cudaSuccess) return cuda_error(e, "tensor map encode");
-      gi.half_begin = halves;
-      halves += (r->nblocks[p] + 63) / 64;
+      const int i = r->direct ? id++ : is++;
+      GroupItem &gi = sl.h_items[i];
+      memcpy(hb + q0 + (size_t)i * kQBytes, r->q[p], kQBytes);
+      const uint16_t *dq = reinterpret_cast<const uint16_t *>(db + q0 + (size_t)i * kQBytes);
+      if (r->direct) {
+        e = fill_group_item_host(&gi, r->op->op, r->din[p], r->dout[p], r->nblocks[p], dq, dq);
+        gi.half_begin = hd;
+        hd += (r->nblocks[p] + 63) / 64;
+      } else {
+        e = fill_group_item(&gi, r->op->op, s->d_arena + r->in_off[p], s->d_arena + r->out_off[p],
+                            r->nblocks[p], true, dq, dq);
+        gi.half_begin = hs;
+        hs += (r->nblocks[p] + 63) / 64;
+      }
+      if (e != cudaSuccess) return cuda_error(e, "batch descriptor");
     }
   }
+  *sl.h_err = 0;
   if (nitems > 0) {
-    *sl.h_err = 0;
-    cudaError_t e = cudaMemcpyAsync(sl.d_items, sl.h_items, nitems * sizeof(GroupItem),
-                                    cudaMemcpyHostToDevice, sl.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_err, 0, sizeof(uint32_t), sl.stream);
-    if (e == cudaSuccess)
-      e = launch_apply_group(sl.d_items, nullptr, nitems, halves, true, s->sms, 2, sl.d_err,
-                             sl.stream);
+    *reinterpret_cast<uint32_t *>(hb + err_off) = 0;
+    e = cudaMemcpyAsync(db, hb, err_off + sizeof(uint32_t), cudaMemcpyHostToDevice, sl.stream);
+    if (e == cudaSuccess && ndirect > 0)
+      e = launch_apply_group_host(sl.d_items, ndirect, hd, kDirectCtas, d_err, sl.stream);
+    if (e == cudaSuccess && nitems > ndirect)
+      e = launch_apply_group(sl.d_items + ndirect, nullptr, nitems - ndirect, hs, true, s->sms, 2,
+                             d_err, sl.stream);
     for (Req *r : batch) {
-      if (e != cudaSuccess || r->status != DCTF_OK) continue;
+      if (e != cudaSuccess || r->status != DCTF_OK || r->direct) continue;
       if (r->out_pinned) {
         for (int p = 0; p < r->nplanes && e == cudaSuccess; ++p)
           e = cudaMemcpyAsync(r->out[p], s->d_arena + r->out_off[p], (size_t)r->nblocks[p] * 128,
@@ -339,10 +400,8 @@ dctf_status launch_batch(dctf_server *s, Slot &sl, std::vector<Req *> &batch) {
       }
     }
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, sl.stream);
+      e = cudaMemcpyAsync(sl.h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, sl.stream);
     if (e != cudaSuccess) return cuda_error(e, "batch launch");
-  } else {
-    *sl.h_err = 0;
   }
   if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
     return set_error(DCTF_ECUDA, "batch event");
@@ -373,7 +432,7 @@ void worker_loop(dctf_server *s) {
         while (!s->pending.empty() && (int)batch.size() < s->cfg.max_batch_requests) {
           Req *r = s->pending.front();
           if (planes + r->nplanes > free_slot->cap) break;
-          if (!s->arena.alloc(r->bytes, &r->off)) break;     // wait for memory
+          if (r->bytes > 0 && !s->arena.alloc(r->bytes, &r->off)) break;   // wait for memory
           s->pending.pop_front();
           planes += r->nplanes;
           batch.push_back(r);
@@ -389,9 +448,9 @@ void worker_loop(dctf_server *s) {
       }
     }
     for (Req *r : batch) {   // arena offsets are known now
+      if (r->direct) continue;
       size_t o = r->off;
       for (int p = 0; p < r->nplanes; ++p) { r->in_off[p] = o; o += round_up(r->nblocks[p] * 128); }
-      for (int p = 0; p < r->nplanes; ++p) { r->q_off[p] = o; o += kAlign; }
       r->in_bytes = o - r->off;
       r->out_start = o;
       for (int p = 0; p < r->nplanes; ++p) { r->out_off[p] = o; o += round_up(r->nblocks[p] * 128); }
@@ -414,7 +473,7 @@ void worker_loop(dctf_server *s) {
 
 size_t request_bytes(const dctf_request *rq) {
   size_t b = 0;
-  for (int p = 0; p < rq->nplanes; ++p) b += 2 * round_up(rq->nblocks[p] * 128) + kAlign;
+  for (int p = 0; p < rq->nplanes; ++p) b += 2 * round_up(rq->nblocks[p] * 128);
   return b;
 }
 
@@ -448,12 +507,10 @@ dctf_status dctf_server_create(const dctf_server_cfg *cfg, dctf_server **out) {
     sl.cap = cap;
     e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_items, cap * sizeof(GroupItem), cudaHostAllocDefault);
+    const size_t ub = (size_t)cap * (sizeof(GroupItem) + kQBytes) + 256;
+    if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_items, ub, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_err, 64, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(&sl.d_items, cap * sizeof(GroupItem) + 256);
-    if (e == cudaSuccess)
-      sl.d_err = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(sl.d_items) +
-                                              cap * sizeof(GroupItem));
+    if (e == cudaSuccess) e = cudaMalloc(&sl.d_items, ub);
   }
   if (e != cudaSuccess) {
     dctf_server_destroy(s);
@@ -478,10 +535,6 @@ dctf_status dctf_server_submit(dctf_server *s, const dctf_request *rq, uint64_t 
       rq->anchor[0] < 0 || rq->anchor[0] >= rq->mh || rq->anchor[1] < 0 ||
       rq->anchor[1] >= rq->mw || (rq->boundary != DCTF_ZERO && rq->boundary != DCTF_REPLICATE))
     return set_error(DCTF_EINVAL, "bad mask, anchor or boundary");
-  const size_t bytes = request_bytes(rq);
-  if (bytes > s->cfg.hbm_budget_bytes)
-    return set_error(DCTF_EBUDGET, "request needs %zu bytes of HBM, budget is %zu", bytes,
-                     (size_t)s->cfg.hbm_budget_bytes);
   Req *r = new (std::nothrow) Req();
   if (r == nullptr) return set_error(DCTF_ENOMEM, "host allocation failed");
   r->nplanes = rq->nplanes;
@@ -495,9 +548,16 @@ dctf_status dctf_server_submit(dctf_server *s, const dctf_request *rq, uint64_t 
   r->key.mh = rq->mh; r->key.mw = rq->mw;
   r->key.ar = rq->anchor[0]; r->key.ac = rq->anchor[1];
   r->key.boundary = rq->boundary;
-  r->bytes = bytes;
+  r->direct = direct_planes(r);
+  r->bytes = r->direct ? 0 : request_bytes(rq);
+  if (r->bytes > s->cfg.hbm_budget_bytes) {
+    const size_t b = r->bytes;
+    delete r;
+    return set_error(DCTF_EBUDGET, "request needs %zu bytes of HBM, budget is %zu", b,
+                     (size_t)s->cfg.hbm_budget_bytes);
+  }
   r->in_pinned = r->out_pinned = true;
-  for (int p = 0; p < rq->nplanes; ++p) {
+  for (int p = 0; p < rq->nplanes && !r->direct; ++p) {
     r->in_pinned = r->in_pinned && is_pinned(rq->in[p]);
     r->out_pinned = r->out_pinned && is_pinned(rq->out[p]);
   }
@@ -555,6 +615,7 @@ dctf_status dctf_server_stats(dctf_server *s, dctf_stats *out) {
   out->max_batch_requests_seen = s->max_batch_seen;
   out->wall_s = s->t_last_done > s->t_first_submit ? (s->t_last_done - s->t_first_submit) / 1e3 : 0;
   out->hbm_in_use = s->arena.used();
+  out->direct_requests = s->direct;
   return DCTF_OK;
 }
 

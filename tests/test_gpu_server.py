@@ -121,12 +121,21 @@ def test_injected_build_failure(dctf, requests):
     srv.close()
 
 
+def staged_result(srv, planes, w, a, bnd):
+    """The request on pageable buffers: the staged route."""
+    outs = [np.zeros_like(p[0]) for p in planes]
+    srv.wait(srv.submit([p[0] for p in planes], outs, [p[1] for p in planes], w, a, bnd))
+    return outs
+
+
 def test_pinned_buffers_take_the_direct_path(dctf, requests):
-    """Page-locked caller buffers are copied by DMA without staging; the
-    results are bit-identical to the staged path."""
+    """Page-locked caller buffers take the host-direct route (the batch
+    kernel reads and writes them over the host link, no HBM staging); the
+    results are bit-identical to the staged route, whether the two kinds of
+    request share a batch or not."""
     srv = dctf.Server(hbm_budget_bytes=64 << 20, max_inflight=2, max_batch_requests=4)
     keep = []
-    for planes, w, a, bnd in requests[:4]:
+    for planes, w, a, bnd in requests[:6]:
         pin_in = [torch.from_numpy(p[0]).pin_memory() for p in planes]
         pin_out = [torch.zeros_like(t).pin_memory() for t in pin_in]
         keep += pin_in + pin_out
@@ -138,5 +147,47 @@ def test_pinned_buffers_take_the_direct_path(dctf, requests):
         srv.wait(t2)
         for tp, o in zip(pin_out, outs):
             assert np.array_equal(tp.numpy(), o)
-    assert srv.stats()["failed"] == 0
+    st = srv.stats()
+    assert st["failed"] == 0 and st["direct_requests"] == 6 and st["completed"] == 12
+    assert st["hbm_in_use"] == 0
     srv.close()
+
+
+def test_direct_in_place_overlap_and_budget(dctf, requests):
+    """In place (out == in) stays host-direct; a request whose planes'
+    buffers overlap otherwise takes the staged route (inputs read before any
+    output is written); a host-direct request needs none of the HBM budget."""
+    srv = dctf.Server(hbm_budget_bytes=1 << 20, max_inflight=2, max_batch_requests=4)
+    ref = dctf.Server(hbm_budget_bytes=64 << 20, max_inflight=1, max_batch_requests=1)
+    planes, w, a, bnd = next(r for r in requests if len(r[0]) == 3)
+    want = staged_result(ref, planes, w, a, bnd)
+    buf = [torch.from_numpy(p[0].copy()).pin_memory() for p in planes]
+    srv.wait(srv.submit([b.numpy() for b in buf], [b.numpy() for b in buf],
+                        [p[1] for p in planes], w, a, bnd))
+    for b, o in zip(buf, want):
+        assert np.array_equal(b.numpy(), o)
+    assert srv.stats()["direct_requests"] == 1
+    # planes 1 and 2 (same size): plane 2's output is plane 1's input buffer
+    p1 = torch.from_numpy(planes[1][0].copy()).pin_memory()
+    p2 = torch.from_numpy(planes[2][0].copy()).pin_memory()
+    o1 = torch.zeros_like(p1).pin_memory()
+    srv.wait(srv.submit([p1.numpy(), p2.numpy()], [o1.numpy(), p1.numpy()],
+                        [planes[1][1], planes[2][1]], w, a, bnd))
+    assert np.array_equal(o1.numpy(), want[1]) and np.array_equal(p1.numpy(), want[2])
+    assert srv.stats()["direct_requests"] == 1                # staged
+    # 2.5 MiB of int16 planes in and out against a 1 MiB budget
+    g = np.random.default_rng(5)
+    x = g.integers(-300, 300, (20480, 64)).astype(np.int16)
+    q = planes[0][1]
+    big = [(x, q)]
+    want_big = staged_result(ref, big, w, a, bnd)
+    hin = torch.from_numpy(x).pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    srv.wait(srv.submit([hin.numpy()], [hout.numpy()], [q], w, a, bnd))
+    assert np.array_equal(hout.numpy(), want_big[0])
+    with pytest.raises(dctf.DctfError):
+        srv.submit([x], [np.zeros_like(x)], [q], w, a, bnd)     # staged: over the budget
+    st = srv.stats()
+    assert st["failed"] == 0 and st["direct_requests"] == 2 and st["hbm_in_use"] == 0
+    srv.close()
+    ref.close()
