@@ -46,7 +46,7 @@ GRAPH_STEPS = 200       # steps per captured graph; the timed loop replays sever
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "adbff8365050c3efec30d9026f5030be3ab3b926": 131936973,
+    "adbff8365050c3efec30d9026f5030be3ab3b926": 131911578,
 }
 
 
