@@ -130,7 +130,7 @@ using namespace dctf;
 
 extern "C" {
 
-int dctf_version(void) { return 200; }   // 0.2.0
+int dctf_version(void) { return 300; }   // 0.3.0
 
 const char *dctf_last_error(void) { return g_last_error.c_str(); }
 

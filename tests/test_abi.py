@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(so):
 
 
 def test_version(so):
-    assert lib.version() >= 200      # 0.2: host-direct apply, grouped pixels, BF16X3
+    assert lib.version() >= 300      # 0.3: host-direct server route (dctf_stats.direct_requests)
 
 
 def build(mask, mh, mw, anchor, n, boundary):
