@@ -158,6 +158,86 @@ def cpu_oracle_sample(job, x, n_sample: int, reps_target_s: float):
     return reps * n_sample / dt, reps, dt
 
 
+_ONE_THREAD_CHILD = """
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+a = json.loads(sys.argv[2])
+x = np.load(a["path"]).astype(np.float64)
+w = np.array(a["mask"])
+t0 = time.perf_counter(); reps = 0
+while True:
+    oracle.apply_M(oracle.build_M(w, tuple(a["anchor"]), 8, a["boundary"]), x)
+    reps += 1
+    if time.perf_counter() - t0 >= a["seconds"]:
+        break
+print(json.dumps({"value": reps * x.shape[0] / (time.perf_counter() - t0), "reps": reps}))
+"""
+
+
+def cpu_oracle_one_thread(job, x, n_sample: int, seconds: float):
+    """The oracle sample timed again in a child process limited to one
+    BLAS / OpenMP thread (the thread count is fixed when numpy loads)."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "x.npy")
+        np.save(path, np.ascontiguousarray(x[:n_sample]))
+        arg = json.dumps({"path": path, "mask": np.asarray(job.mask).tolist(),
+                          "anchor": list(job.anchor), "boundary": int(job.boundary),
+                          "seconds": seconds})
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1", OPENBLAS_MAIN_FREE="1")
+        r = subprocess.run([sys.executable, "-c", _ONE_THREAD_CHILD, os.path.dirname(__file__) or ".",
+                            arg], env=env, capture_output=True, text=True, timeout=10 * seconds + 60)
+        if r.returncode != 0:
+            return {"error": r.stderr.strip().splitlines()[-1:] or ["exit %d" % r.returncode]}
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        out.update({"cores": 1, "sample": f"{out['reps']} x (operator build + apply to {n_sample} "
+                                          f"blocks), one BLAS thread"})
+        return out
+
+
+def cpu_spatial_route(job, n_sample: int, seconds: float):
+    """The oracle's spatial route per block (IDCT, the mask on the padded
+    block, DCT) on a sample of the workload's blocks: the computation the
+    DCT-domain operator replaces."""
+    import oracle
+    blocks = oracle.image_to_blocks(job.image, 8)[:n_sample]
+    coef = oracle.dct2_blocks(blocks)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        px = oracle.idct2_blocks(coef, 8).reshape(-1, 8, 8)
+        oracle.dct2_blocks(oracle.spatial_filter_blocks(px, job.mask, job.anchor, job.boundary))
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": reps * n_sample / dt, "unit": UNIT, "cores": os.cpu_count(),
+            "threads": "numpy elementwise steps on one thread, BLAS default for the DCTs",
+            "sample": f"{reps} x (IDCT + spatial filter + DCT of {n_sample} blocks), numpy FP64"}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def oracle_parity(job, x_sample, y_gpu):
     """Parity of the timed kernel's output with the FP64 oracle on the CPU
     baseline's sample: coefficient error, and uint8 pixels against the
@@ -734,7 +814,10 @@ def run_dctf(args):
         v, reps, dt = cpu_oracle_sample(job, x_host, 65536, 8.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{reps} x (operator build + apply to 65536 of the "
-                                          f"262144 blocks), {dt:.1f} s, numpy FP64"}
+                                          f"262144 blocks), {dt:.1f} s, numpy FP64",
+                                "cpu_model": cpu_model(),
+                                "one_thread": cpu_oracle_one_thread(job, x_host, 16384, 4.0),
+                                "spatial_route": cpu_spatial_route(job, 4096, 4.0)}
         # the timed F16X3 kernel's output on the same sample, checked by the oracle
         ops[0].set_precision(lib.F16X3)
         ops[0].set_flags(0)
