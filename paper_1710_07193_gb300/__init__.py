@@ -392,7 +392,9 @@ class Server:
     def prepare(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int):
         """Marshal one request (argument conversion only) for submit_prepared.
         planes_in/out: host int16 arrays [nblocks][64] (kept alive until the
-        request is waited for); qtabs: uint16 [64] per plane."""
+        request is waited for); qtabs: uint16 [64] per plane.  Page-locked
+        planes (e.g. views of torch pinned tensors) take the server's
+        host-direct route."""
         r = _Request()
         r.nplanes = len(planes_in)
         keep = [np.ascontiguousarray(mask, dtype=np.float64)]
