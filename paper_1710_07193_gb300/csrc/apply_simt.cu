@@ -11,9 +11,11 @@
 // once to an accumulator of the AC terms keeps the rounding error of the
 // sums near one ulp of the output instead of growing with the DC magnitude.
 #include "dctf_internal.cuh"
+#include "sm100_ptx.cuh"
 
 namespace dctf {
 namespace {
+using namespace ptx;
 
 template <typename Tin> __device__ inline float4 load4(const Tin *p);
 template <> __device__ inline float4 load4<float>(const float *p) {
@@ -135,6 +137,129 @@ apply_simt_kernel(const float *__restrict__ M32, const float *__restrict__ Mdc,
   }
 }
 
+// FP32 input, M resident (TN = TK = N2): the same tile walk and arithmetic
+// as apply_simt_kernel, but the next tile's input streams into a second X
+// buffer with cp.async while the current tile computes, so the tile loads
+// leave the critical path.  Each output sums the same terms in the same
+// order: the bits equal apply_simt_kernel's.
+template <int N2, int TB, int RB, int RN>
+struct SimtDbCfg {
+  static constexpr int kThreads = (TB / RB) * (N2 / RN);
+  static constexpr int kXP = N2 + 4;
+  static constexpr int kXFloats = TB * kXP;
+  static constexpr size_t kSmem = (size_t)(2 * kXFloats + N2 * kXP + TB) * 4;
+  static_assert(kThreads == 128 && TB == 128, "128 threads, one tile row each");
+};
+
+template <int N2, int TB, int RB, int RN>
+__global__ void __launch_bounds__(128)
+apply_simt_db_kernel(const float *__restrict__ M32, const float *__restrict__ Mdc,
+                     const float *__restrict__ x, int64_t nblocks, float *y) {
+  using Cfg = SimtDbCfg<N2, TB, RB, RN>;
+  constexpr int kXP = Cfg::kXP;
+  constexpr int TPB = TB / RB, TPN = N2 / RN;
+  extern __shared__ __align__(16) float smem[];
+  float *Ms = smem + 2 * Cfg::kXFloats;
+  float *x0s = Ms + N2 * kXP;
+  const int t = threadIdx.x, tb = t / TPN, tn = t % TPN;
+  const int64_t ntiles = (nblocks + TB - 1) / TB;
+
+  for (int idx = t; idx < N2 * N2 / 4; idx += 128) {
+    int r = idx / (N2 / 4), c4 = idx % (N2 / 4);
+    *reinterpret_cast<float4 *>(&Ms[r * kXP + 4 * c4]) =
+        __ldg(reinterpret_cast<const float4 *>(M32 + (size_t)r * N2) + c4);
+  }
+  // tile `tl` into buffer `buf`: 16-byte copies, zero-filled past nblocks
+  auto issue = [&](int64_t tl, int buf) {
+    float *dst = smem + buf * Cfg::kXFloats;
+    const int64_t b0 = tl * TB;
+    for (int idx = t; idx < TB * N2 / 4; idx += 128) {
+      const int r = idx / (N2 / 4), c4 = idx % (N2 / 4);
+      const bool ok = b0 + r < nblocks;
+      cp_async_16(smem_u32(dst + r * kXP + 4 * c4), ok ? x + (b0 + r) * N2 + 4 * c4 : x,
+                  ok ? 16u : 0u);
+    }
+    cp_async_commit();
+  };
+
+  int c = 0;
+  if ((int64_t)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, c ^= 1) {
+    const int64_t b0 = tile * TB;
+    float *Xs = smem + c * Cfg::kXFloats;
+    __syncthreads();   // the previous tile's output stores have read buffer c ^ 1
+    const bool more = tile + gridDim.x < ntiles;
+    if (more) issue(tile + gridDim.x, c ^ 1);
+    if (more) cp_async_wait_group<1>(); else cp_async_wait_group<0>();
+    __syncthreads();   // every thread's copies of this tile have landed
+    x0s[t] = Xs[t * kXP];   // the DC input term, added last
+    Xs[t * kXP] = 0.f;
+    __syncthreads();
+    float acc[RB][RN];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
+    for (int k4 = 0; k4 < N2; k4 += 4) {
+      float4 xa[RB], ma[RN];
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        xa[i] = *reinterpret_cast<const float4 *>(&Xs[(tb + TPB * i) * kXP + k4]);
+#pragma unroll
+      for (int j = 0; j < RN; ++j)
+        ma[j] = *reinterpret_cast<const float4 *>(&Ms[(tn + TPN * j) * kXP + k4]);
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) {
+          acc[i][j] = fmaf(xa[i].x, ma[j].x, acc[i][j]);
+          acc[i][j] = fmaf(xa[i].y, ma[j].y, acc[i][j]);
+          acc[i][j] = fmaf(xa[i].z, ma[j].z, acc[i][j]);
+          acc[i][j] = fmaf(xa[i].w, ma[j].w, acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      float md = __ldg(Mdc + tn + TPN * j);
+#pragma unroll
+      for (int i = 0; i < RB; ++i) acc[i][j] = fmaf(md, x0s[tb + TPB * i], acc[i][j]);
+    }
+    __syncthreads();   // all reads of Xs done: it stages the outputs now
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) Xs[(tb + TPB * i) * kXP + tn + TPN * j] = acc[i][j];
+    __syncthreads();
+    for (int idx = t; idx < TB * N2 / 4; idx += 128) {
+      int r = idx / (N2 / 4), c4 = idx % (N2 / 4);
+      if (b0 + r < nblocks)
+        *reinterpret_cast<float4 *>(y + (b0 + r) * N2 + 4 * c4) =
+            *reinterpret_cast<const float4 *>(&Xs[r * kXP + 4 * c4]);
+    }
+  }
+}
+
+template <int N2, int TB, int RB, int RN>
+cudaError_t launch_db(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
+                      cudaStream_t s) {
+  using Cfg = SimtDbCfg<N2, TB, RB, RN>;
+  auto kern = apply_simt_db_kernel<N2, TB, RB, RN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Cfg::kSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, Cfg::kSmem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t ntiles = (nblocks + TB - 1) / TB;
+  int64_t grid = (int64_t)per_sm * sm_count(op->device);
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, 128, Cfg::kSmem, s>>>(op->d_M32, op->d_Mdc, x, nblocks, y);
+  return cudaGetLastError();
+}
+
 template <typename Tin, int N2, int TB, int TN, int TK, int RB, int RN>
 cudaError_t launch_cfg(const dctf_operator *op, const Tin *x, int64_t nblocks, float *y,
                        cudaStream_t s) {
@@ -166,6 +291,10 @@ cudaError_t dispatch(const dctf_operator *op, const Tin *x, int64_t nblocks, flo
       // output sums the same K chunks in the same order, so the bits match.
       if (nblocks < (int64_t)128 * sm_count(op->device))
         return launch_cfg<Tin, 64, 16, 64, 64, 2, 4>(op, x, nblocks, y, s);
+      if constexpr (sizeof(Tin) == 4) {
+        // FP32 input (16-byte aligned, checked by the caller): double-buffered
+        return launch_db<64, 128, 8, 8>(op, reinterpret_cast<const float *>(x), nblocks, y, s);
+      }
       return launch_cfg<Tin, 64, 128, 64, 64, 8, 8>(op, x, nblocks, y, s);
     case 16: return launch_cfg<Tin, 256, 32, 128, 64, 4, 8>(op, x, nblocks, y, s);
   }

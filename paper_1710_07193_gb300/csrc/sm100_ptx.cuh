@@ -175,6 +175,14 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// Close this thread's current group of cp.async copies / wait until at
+// most N of its groups are still in flight.
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 // Make this thread's generic-proxy shared-memory writes visible to the
 // async proxy (TMA stores, tcgen05.mma operand reads).
 __device__ __forceinline__ void fence_async_smem() {
