@@ -10,6 +10,9 @@
 // last as M[:,0] x_b[0]: it is the largest coefficient by far, and adding it
 // once to an accumulator of the AC terms keeps the rounding error of the
 // sums near one ulp of the output instead of growing with the DC magnitude.
+// For 8x8 blocks with FP32 input at full size, apply_simt_db_kernel runs the
+// same arithmetic with the next tile's loads overlapped (cp.async into a
+// second X buffer).
 #include "dctf_internal.cuh"
 #include "sm100_ptx.cuh"
 
@@ -291,11 +294,11 @@ cudaError_t dispatch(const dctf_operator *op, const Tin *x, int64_t nblocks, flo
       // output sums the same K chunks in the same order, so the bits match.
       if (nblocks < (int64_t)128 * sm_count(op->device))
         return launch_cfg<Tin, 64, 16, 64, 64, 2, 4>(op, x, nblocks, y, s);
-      if constexpr (sizeof(Tin) == 4) {
-        // FP32 input (16-byte aligned, checked by the caller): double-buffered
+      // FP32 input (16-byte aligned, checked by the caller): double-buffered
+      if constexpr (sizeof(Tin) == 4)
         return launch_db<64, 128, 8, 8>(op, reinterpret_cast<const float *>(x), nblocks, y, s);
-      }
-      return launch_cfg<Tin, 64, 128, 64, 64, 8, 8>(op, x, nblocks, y, s);
+      else
+        return launch_cfg<Tin, 64, 128, 64, 64, 8, 8>(op, x, nblocks, y, s);
     case 16: return launch_cfg<Tin, 256, 32, 128, 64, 4, 8>(op, x, nblocks, y, s);
   }
   return cudaErrorInvalidValue;
