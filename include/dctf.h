@@ -39,6 +39,7 @@
 #ifndef DCTF_H
 #define DCTF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -202,11 +203,13 @@ dctf_status dctf_apply_pixels(const dctf_operator *op, const float *coeffs,
                               int height, int width, uint8_t *image,
                               int64_t pitch, dctf_stream_t stream);
 
-/* dctf_apply for coefficients in the image-plane layout (a JPEG decoder's
- * coefficient plane): an FP32 array shaped like the pixel image, where
- * coefficient (u, v) of block (by, bx) sits at row 8 by + u, column 8 bx + v.
- * The kernel reads and writes it with 4-D TMA boxes (no layout conversion
- * pass).  Same arithmetic as dctf_apply (F16X3 tensor cores).
+/* dctf_apply (y_b = M x_b, Eq. 11 / Eq. 20) for coefficients in the
+ * image-plane layout (a JPEG decoder's coefficient plane): an FP32 array
+ * shaped like the pixel image, where coefficient (u, v) of block (by, bx)
+ * sits at row 8 by + u, column 8 bx + v.  The kernel reads and writes it with
+ * 2-D TMA boxes of 256 floats x 8 rows (32 blocks of one block row; no
+ * layout conversion pass).  Same arithmetic as dctf_apply (F16X3 tensor
+ * cores).
  *  coeffs, out  device FP32, height rows of pitch / out_pitch floats
  *               (pitches >= width, multiples of 4; 16-byte aligned); only
  *               the height x width coefficients are written.  out == coeffs
@@ -217,14 +220,15 @@ dctf_status dctf_apply_planar(const dctf_operator *op, const float *coeffs,
                               int height, int width, int64_t pitch, float *out,
                               int64_t out_pitch, dctf_stream_t stream);
 
-/* As dctf_apply, with FP64 input coefficients (FP32 output), FP32 SIMT
- * arithmetic; for the small FP64-coefficient workload. */
+/* As dctf_apply (y_b = M x_b, Eq. 11 / Eq. 20), with FP64 input
+ * coefficients (FP32 output), FP32 SIMT arithmetic; for the small
+ * FP64-coefficient workload. */
 dctf_status dctf_apply_f64in(const dctf_operator *op, const double *coeffs,
                              int64_t nblocks, float *out,
                              dctf_stream_t stream);
 
 /* End-to-end call for callers holding the data in HOST memory (the same
- * y_b = M x_b as dctf_apply).  host_in, host_out: [nblocks][N*N] FP32 in
+ * y_b = M x_b as dctf_apply, Eq. 11 / Eq. 20).  host_in, host_out: [nblocks][N*N] FP32 in
  * host memory, owned by the caller; host_out == host_in allowed, no other
  * overlap (EINVAL).  Two routes, chosen per call:
  *  - 8x8 DCTF_F16X3 with both buffers page-locked and mapped (cudaHostAlloc,
@@ -380,8 +384,10 @@ typedef struct dctf_server dctf_server;
  * slots on the current device; start the worker thread. */
 dctf_status dctf_server_create(const dctf_server_cfg *cfg, dctf_server **out);
 
-/* Queue a request; its host buffers must stay valid until dctf_server_wait
- * returns for its ticket.  Routes, chosen per request at submit:
+/* Queue a request: every plane is dequantised, filtered block by block
+ * (y_b = M x_b, Eq. 11 / Eq. 20) and requantised with its own table.  Its
+ * host buffers must stay valid until dctf_server_wait returns for its
+ * ticket.  Routes, chosen per request at submit:
  *  - host-direct: every plane's input and output is page-locked, mapped
  *    memory (cudaHostAlloc, cudaHostRegister), 16-byte aligned, and no two
  *    of the request's buffers overlap except a plane filtered in place
@@ -416,9 +422,11 @@ dctf_status dctf_forward_dct_f64(const uint8_t *image, int height, int width,
                                  int64_t pitch, int n, double *coeffs,
                                  dctf_stream_t stream);
 
-/* Forward DCT followed by JPEG-style quantisation with a per-coefficient
- * table q (device, n*n entries): coeffs[b][k] = sat_int16(round_half_away(
- * BLOCK[k] / q[k])).  Prepares int16 input for the quantised grouped path. */
+/* Forward DCT (Sec. II.A, Eq. 1) followed by JPEG-style quantisation with a
+ * per-coefficient table q (device, n*n entries; the quantisation is codec
+ * practice, not part of the paper): coeffs[b][k] = sat_int16(
+ * round_half_away(BLOCK[k] / q[k])).  Prepares int16 input for the
+ * quantised grouped path. */
 dctf_status dctf_forward_dct_i16(const uint8_t *image, int height, int width,
                                  int64_t pitch, int n, const uint16_t *q,
                                  int16_t *coeffs, dctf_stream_t stream);
@@ -430,8 +438,9 @@ dctf_status dctf_inverse_dct_u8(const float *coeffs, int height, int width,
                                 int n, uint8_t *image, int64_t pitch,
                                 dctf_stream_t stream);
 
-/* Build the FP64 operator M (and optionally H) for one mask into memory the
- * caller provides, allocating nothing.  The paper has no counterpart: this
+/* Build the FP64 operator M = K H K^T (Eq. 7; H the per-block spatial filter
+ * of Sec. II.B-C, as dctf_build_operator) and optionally H for one mask into
+ * memory the caller provides, allocating nothing.  The paper has no counterpart: this
  * exists for callers that cannot call cudaMalloc -- code inside a framework
  * whose pool owns all device memory, real-time paths where cudaMalloc's
  * implicit device synchronisation is not allowed, plug-ins that are handed

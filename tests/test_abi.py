@@ -4,6 +4,8 @@ import ctypes
 import glob
 import os
 import re
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
@@ -37,6 +39,21 @@ def test_every_declared_symbol_is_exported(so):
     for n in sorted(names):
         assert hasattr(so, n), n
     assert names == set(lib.exported_symbols())
+
+
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_headers_compile_standalone(lang, tmp_path):
+    """Each public header compiles on its own, first in its translation unit,
+    as C and as C++ (no CUDA headers needed)."""
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = tmp_path / ("t.c" if lang == "c" else "t.cpp")
+        src.write_text('#include "%s"\nint main(void) { return 0; }\n' % os.path.basename(h))
+        r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                            str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
 
 
 def test_version(so):
