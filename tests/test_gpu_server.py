@@ -45,13 +45,19 @@ def run_one(srv, req):
 
 
 def test_alone_equals_mixed_and_oracle(dctf, requests):
-    srv = dctf.Server(hbm_budget_bytes=64 << 20, max_inflight=3, max_batch_requests=4)
+    srv = dctf.Server(hbm_budget_bytes=512 << 20, max_inflight=2, max_batch_requests=4)
     alone = []
     for req in requests:
         t, outs = run_one(srv, req)
         srv.wait(t)
         alone.append(outs)
+    # the burst arrives while the worker stages a 64 MB pageable request
+    # (milliseconds of host copying), so it queues and must be batched
+    big = np.zeros((1 << 19, 64), dtype=np.int16)
+    w0, a0, b0 = requests[0][1:]
+    t_big = srv.submit([big], [np.empty_like(big)], [requests[0][0][0][1]], w0, a0, b0)
     burst = [run_one(srv, req) for req in requests]
+    srv.wait(t_big)
     for t, _ in burst:
         srv.wait(t)
     for (planes, w, a, bnd), outs_alone, (_, outs_mix) in zip(requests, alone, burst):
@@ -62,7 +68,7 @@ def test_alone_equals_mixed_and_oracle(dctf, requests):
             st = oracle.int16_compare(v, ya, BAND)
             assert st["mismatch"] == 0, st
     st = srv.stats()
-    assert st["completed"] == 2 * len(requests) and st["failed"] == 0
+    assert st["completed"] == 2 * len(requests) + 1 and st["failed"] == 0
     assert st["cache_hits"] > 0 and 0 < st["p50_ms"] <= st["p99_ms"]
     assert st["max_batch_requests_seen"] > 1          # the burst really batched
     assert st["hbm_in_use"] == 0
