@@ -144,3 +144,81 @@ def test_kron_mutant_is_caught(name, monkeypatch):
         except AssertionError:
             failures += 1
     assert failures > 0, f"mutant {name} passed every pin"
+
+
+# ----------------------------------------------------- int16 serving path
+from tests import test_oracle_int16 as t_i16  # noqa: E402
+
+_orig_serve = od.serve_blocks
+
+
+def serve_swapped_tables(q_in, qtab_in, m, qtab_out):
+    return _orig_serve(q_in, qtab_out, m, qtab_in)
+
+
+def serve_transposed_M(q_in, qtab_in, m, qtab_out):
+    return _orig_serve(q_in, qtab_in, np.asarray(m).T, qtab_out)
+
+
+def requantise_half_even(y, qtab):
+    v = np.asarray(y, dtype=np.float64) / np.asarray(qtab, dtype=np.float64).ravel()[None, :]
+    return np.clip(np.round(v), -32768, 32767).astype(np.int16)
+
+
+def cmp_wrong_saturation(v_ref, q_test, band=1e-4):
+    # the saturation bound of the reference rounding off by one at the bottom
+    v = np.asarray(v_ref, dtype=np.float64).ravel()
+    t = np.asarray(q_test).ravel()
+    frac = np.abs(v - np.floor(v) - 0.5)
+    inside = (frac < band) & (v > -32768.5 - band) & (v < 32767.5 + band)
+    ref = np.clip(oracle.round_half_away(v), -32767, 32767)
+    bad = (ref != t) & ~inside
+    return {"mismatch": int(bad.sum()), "band": int(inside.sum()), "total": int(v.size)}
+
+
+def cmp_wide_band_edge(v_ref, q_test, band=1e-4):
+    # ties counted past the saturation edge, where both neighbours saturate
+    v = np.asarray(v_ref, dtype=np.float64).ravel()
+    t = np.asarray(q_test).ravel()
+    frac = np.abs(v - np.floor(v) - 0.5)
+    inside = (frac < band) & (v > -32769.5 - band) & (v < 32768.5 + band)
+    ref = np.clip(oracle.round_half_away(v), -32768, 32767)
+    bad = (ref != t) & ~inside
+    return {"mismatch": int(bad.sum()), "band": int(inside.sum()), "total": int(v.size)}
+
+
+I16_MUTANTS = {
+    "serve_swapped_tables": ("serve_blocks", serve_swapped_tables),
+    "serve_transposed_M": ("serve_blocks", serve_transposed_M),
+    "requantise_half_even": ("requantise", requantise_half_even),
+    "compare_wrong_saturation": ("int16_compare", cmp_wrong_saturation),
+    "compare_wide_band_edge": ("int16_compare", cmp_wide_band_edge),
+}
+
+
+def _i16_pins():
+    return [
+        t_i16.test_serve_blocks_hand_computed,
+        t_i16.test_serve_blocks_tables_not_interchangeable,
+        t_i16.test_serve_blocks_dc_only_block_replicate,
+        t_i16.test_int16_compare_saturation_and_band,
+    ]
+
+
+@pytest.mark.parametrize("name", sorted(I16_MUTANTS))
+def test_int16_mutant_is_caught(name, monkeypatch):
+    attr, fn = I16_MUTANTS[name]
+    monkeypatch.setattr(od, attr, fn)
+    monkeypatch.setattr(oracle, attr, fn)
+    failures = 0
+    for pin in _i16_pins():
+        try:
+            pin()
+        except AssertionError:
+            failures += 1
+    assert failures > 0, f"mutant {name} passed every pin"
+
+
+def test_unmutated_int16_oracle_passes_every_pin():
+    for pin in _i16_pins():
+        pin()
