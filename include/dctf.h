@@ -355,6 +355,9 @@ typedef struct {
     int max_batch_requests;         /* requests per batch (>= 1)                  */
     int op_cache_capacity;          /* cached operators (>= 1)                    */
     int inject_build_failure_every; /* test hook: fail every k-th build (0 off)   */
+    int staged_only;                /* nonzero: every request takes the staged    */
+                                    /* route (HBM arena, admission by the budget), */
+                                    /* page-locked planes included                 */
 } dctf_server_cfg;
 
 typedef struct {
@@ -362,11 +365,15 @@ typedef struct {
     const int16_t *in[4];           /* host [nblocks][64], read during the call... */
     int16_t *out[4];                /* ...and written before wait returns          */
     int64_t nblocks[4];             /* > 0                                         */
-    const uint16_t *q[4];           /* host [64] quantisation table per plane      */
+    const uint16_t *q[4];           /* host [64] quantisation table per plane: the */
+                                    /* input is dequantised with it                */
     const double *mask;             /* host row-major mh x mw, copied at submit    */
     int mh, mw;                     /* 1..8                                        */
     int anchor[2];
     dctf_boundary boundary;
+    const uint16_t *q_out[4];       /* host [64] table the output is requantised   */
+                                    /* with, or NULL for the plane's q (copied at  */
+                                    /* submit)                                     */
 } dctf_request;
 
 typedef struct {
@@ -376,6 +383,11 @@ typedef struct {
     int max_batch_requests_seen;
     size_t hbm_in_use;
     uint64_t direct_requests;                /* completed on the host-direct route */
+    uint64_t budget_waits;                   /* requests that waited for HBM: at the
+                                                head of the queue, with a batch slot
+                                                free, they did not fit the budget's
+                                                free space until others finished  */
+    size_t hbm_peak;                         /* most budget bytes in use at once  */
 } dctf_stats;
 
 typedef struct dctf_server dctf_server;
@@ -384,11 +396,13 @@ typedef struct dctf_server dctf_server;
  * slots on the current device; start the worker thread. */
 dctf_status dctf_server_create(const dctf_server_cfg *cfg, dctf_server **out);
 
-/* Queue a request: every plane is dequantised, filtered block by block
- * (y_b = M x_b, Eq. 11 / Eq. 20) and requantised with its own table.  Its
+/* Queue a request: every plane is dequantised with its table q, filtered
+ * block by block (y_b = M x_b, Eq. 11 / Eq. 20) and requantised with its
+ * table q_out (q when q_out is NULL).  Its
  * host buffers must stay valid until dctf_server_wait returns for its
  * ticket.  Routes, chosen per request at submit:
- *  - host-direct: every plane's input and output is page-locked, mapped
+ *  - host-direct (unless the server was created staged_only): every
+ *    plane's input and output is page-locked, mapped
  *    memory (cudaHostAlloc, cudaHostRegister), 16-byte aligned, and no two
  *    of the request's buffers overlap except a plane filtered in place
  *    (in == out).  The batch kernel reads and writes these planes over the
@@ -438,21 +452,24 @@ dctf_status dctf_inverse_dct_u8(const float *coeffs, int height, int width,
                                 int n, uint8_t *image, int64_t pitch,
                                 dctf_stream_t stream);
 
-/* Build the FP64 operator M = K H K^T (Eq. 7; H the per-block spatial filter
- * of Sec. II.B-C, as dctf_build_operator) and optionally H for one mask into
- * memory the caller provides, allocating nothing.  The paper has no counterpart: this
- * exists for callers that cannot call cudaMalloc -- code inside a framework
- * whose pool owns all device memory, real-time paths where cudaMalloc's
- * implicit device synchronisation is not allowed, plug-ins that are handed
- * only the buffers they read and write.
+/* Allocation-free build: the same FP64 operator M (and optionally the
+ * spatial operator H) that dctf_build_operator makes for one mask, written
+ * into memory the caller provides; the library allocates nothing.  The
+ * paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc -- code inside a framework whose pool owns all device memory,
+ * real-time paths where cudaMalloc's implicit device synchronisation is not
+ * allowed, plug-ins that are handed only the buffers they read and write.
  *  M_out  device, n2*n2 doubles (row = output coefficient), 16-byte aligned.
- *  H_out  device, n2*n2 doubles, or NULL.
- * Same arguments and checks as dctf_build_operator otherwise; asynchronous
- * on `stream`.  The build's scratch is a static 1 MiB device array inside the
- * library (enough for the largest block, n = 16); sizes beyond it are
- * rejected with DCTF_EINVAL.  The first call on a device looks up that
- * array's device address, so make it before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU (different streams, or
+ *  H_out  device, n2*n2 doubles (row = output pixel i*n+j), or NULL.
+ * Same mask, anchor and boundary arguments and checks as
+ * dctf_build_operator; asynchronous on `stream`.  The build's scratch is a
+ * static 1 MiB device array inside the library (2 n^4 doubles: enough for
+ * the largest block, n = 16); a block side beyond it (n > 16) is rejected
+ * with DCTF_EINVAL and a message naming the scratch limit.  The first call
+ * in a CUDA context (the first on a device, or the first after a device
+ * reset) looks up that array's device address, so make it before any
+ * stream capture.  Every call shares the array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams, or
  * several host threads) race and must be serialised by the caller. */
 dctf_status dctf_build_matrix_noalloc(const double *mask, int mh, int mw,
                                       const int anchor[2], int n,

@@ -348,13 +348,13 @@ def apply_grouped(items, io: int = IO_F32, stream=None) -> None:
 class _ServerCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", _i32),
                 ("max_batch_requests", _i32), ("op_cache_capacity", _i32),
-                ("inject_build_failure_every", _i32)]
+                ("inject_build_failure_every", _i32), ("staged_only", _i32)]
 
 
 class _Request(ctypes.Structure):
     _fields_ = [("nplanes", _i32), ("inp", _vp * 4), ("out", _vp * 4), ("nblocks", _i64 * 4),
                 ("q", _vp * 4), ("mask", _vp), ("mh", _i32), ("mw", _i32),
-                ("anchor", _i32 * 2), ("boundary", _i32)]
+                ("anchor", _i32 * 2), ("boundary", _i32), ("q_out", _vp * 4)]
 
 
 class _Stats(ctypes.Structure):
@@ -364,7 +364,8 @@ class _Stats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("blocks", ctypes.c_uint64), ("cache_hits", ctypes.c_uint64),
                 ("cache_misses", ctypes.c_uint64), ("max_batch_requests_seen", _i32),
-                ("hbm_in_use", ctypes.c_size_t), ("direct_requests", ctypes.c_uint64)]
+                ("hbm_in_use", ctypes.c_size_t), ("direct_requests", ctypes.c_uint64),
+                ("budget_waits", ctypes.c_uint64), ("hbm_peak", ctypes.c_size_t)]
 
 
 _SIGS.update({
@@ -381,30 +382,36 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int = 1 << 30, max_inflight: int = 3,
                  max_batch_requests: int = 16, op_cache_capacity: int = 64,
-                 inject_build_failure_every: int = 0):
+                 inject_build_failure_every: int = 0, staged_only: bool = False):
         cfg = _ServerCfg(hbm_budget_bytes, max_inflight, max_batch_requests, op_cache_capacity,
-                         inject_build_failure_every)
+                         inject_build_failure_every, 1 if staged_only else 0)
         h = ctypes.c_void_p(0)
         _check(load().dctf_server_create(ctypes.addressof(cfg), ctypes.addressof(h)))
         self.handle = h.value
         self._keep = {}
 
-    def prepare(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int):
+    def prepare(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int, qtabs_out=None):
         """Marshal one request (argument conversion only) for submit_prepared.
         planes_in/out: host int16 arrays [nblocks][64] (kept alive until the
-        request is waited for); qtabs: uint16 [64] per plane.  Page-locked
-        planes (e.g. views of torch pinned tensors) take the server's
-        host-direct route."""
+        request is waited for); qtabs: uint16 [64] per plane (dequantisation);
+        qtabs_out: uint16 [64] per plane for the requantisation, or None for
+        qtabs.  Page-locked planes (e.g. views of torch pinned tensors) take
+        the server's host-direct route unless it was created staged_only."""
         r = _Request()
         r.nplanes = len(planes_in)
         keep = [np.ascontiguousarray(mask, dtype=np.float64)]
-        for p, (xi, xo, q) in enumerate(zip(planes_in, planes_out, qtabs)):
+        outs = qtabs_out if qtabs_out is not None else [None] * len(planes_in)
+        for p, (xi, xo, q, qo) in enumerate(zip(planes_in, planes_out, qtabs, outs)):
             q = np.ascontiguousarray(q, dtype=np.uint16).ravel()
             keep += [xi, xo, q]
             r.inp[p] = _ptr(xi)
             r.out[p] = _ptr(xo)
             r.nblocks[p] = xi.shape[0]
             r.q[p] = q.ctypes.data
+            if qo is not None:
+                qo = np.ascontiguousarray(qo, dtype=np.uint16).ravel()
+                keep.append(qo)
+                r.q_out[p] = qo.ctypes.data
         r.mask = keep[0].ctypes.data
         r.mh, r.mw = keep[0].shape
         r.anchor[0], r.anchor[1] = anchor
@@ -419,9 +426,11 @@ class Server:
         self._keep[t.value] = keep
         return t.value
 
-    def submit(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int) -> int:
+    def submit(self, planes_in, planes_out, qtabs, mask, anchor, boundary: int,
+               qtabs_out=None) -> int:
         """prepare() + submit_prepared()."""
-        return self.submit_prepared(self.prepare(planes_in, planes_out, qtabs, mask, anchor, boundary))
+        return self.submit_prepared(self.prepare(planes_in, planes_out, qtabs, mask, anchor,
+                                                 boundary, qtabs_out))
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> None:
         st = load().dctf_server_wait(self.handle, ticket, timeout_ms)

@@ -270,24 +270,66 @@ __global__ void build_m_noalloc_kernel(int n, const double *__restrict__ G,
   if (t < n2) M64[(size_t)t * n2 + q] = m;
 }
 
-std::mutex g_scratch_mu;
-double *g_scratch_addr[64];
+// Driver entry points fetched at run time (libcuda is not linked).
+template <class Fn>
+Fn driver_fn(const char *name) {
+  void *f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return reinterpret_cast<Fn>(f);
+  return nullptr;
+}
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
 
-// Device address of the static scratch on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device pointer).
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  double *addr;
+};
+std::mutex g_scratch_mu;
+ScratchAddr g_scratch_addr[64];   // one per context seen; a full table starts over
+int g_scratch_n = 0;
+
+// Device address of the static scratch in the current context.  Host code
+// cannot use the symbol itself as a device pointer: the address is looked up
+// with cudaGetSymbolAddress once per context (the first call on a device)
+// and cached under the context's ID, which CUDA never reuses within a
+// process, so a context made after a device reset gets its own lookup.
 cudaError_t scratch_on_current_device(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (g_scratch_addr[dev] == nullptr) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, dctf_build_scratch);
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    get_cur = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+    get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  });
+  if (get_cur == nullptr || get_id == nullptr) return cudaErrorNotSupported;
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (ctx == nullptr) {
+    // no context on this thread yet: make the current device's primary
+    // context current (cudaSetDevice initialises it; nothing is allocated)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double *>(p);
+    if (get_cur(&ctx) != CUDA_SUCCESS || ctx == nullptr) return cudaErrorDeviceUninitialized;
   }
-  *out = g_scratch_addr[dev];
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  for (int i = 0; i < g_scratch_n; ++i)
+    if (g_scratch_addr[i].ctx_id == id) {
+      *out = g_scratch_addr[i].addr;
+      return cudaSuccess;
+    }
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, dctf_build_scratch);
+  if (e != cudaSuccess) return e;
+  if (g_scratch_n == 64) g_scratch_n = 0;
+  g_scratch_addr[g_scratch_n++] = {id, static_cast<double *>(p)};
+  *out = static_cast<double *>(p);
   return cudaSuccess;
 }
 
@@ -299,33 +341,24 @@ extern "C" dctf_status dctf_build_matrix_noalloc(const double *mask, int mh, int
                                                  dctf_boundary boundary, double *M_out,
                                                  double *H_out, dctf_stream_t stream) {
   using namespace dctf;
-  if (n != 4 && n != 8 && n != 16)
-    return set_error(DCTF_EINVAL, "block size n=%d: must be 4, 8 or 16", n);
+  // the scratch holds G and H, 2 n^4 doubles: a block side beyond its size
+  // is refused before anything else is looked at
+  if (n < 1) return set_error(DCTF_EINVAL, "block size n=%d: must be positive", n);
   const size_t n2 = (size_t)n * n;
-  if (2 * n2 * n2 > kScratchDoubles)
-    return set_error(DCTF_EINVAL, "n=%d needs %zu scratch doubles; the static scratch holds %zu",
-                     n, 2 * n2 * n2, kScratchDoubles);
-  if (mask == nullptr || anchor == nullptr || M_out == nullptr)
-    return set_error(DCTF_EINVAL, "mask, anchor and M_out must not be NULL");
+  if (n > kMaxN || 2 * n2 * n2 > kScratchDoubles)
+    return set_error(DCTF_EINVAL,
+                     "n=%d needs %zu doubles of build scratch; the static scratch holds %zu "
+                     "(n <= %d)",
+                     n, 2 * n2 * n2, kScratchDoubles, kMaxN);
+  MaskParams mp;
+  const dctf_status st = check_mask(mask, mh, mw, anchor, n, boundary, &mp);
+  if (st != DCTF_OK) return st;
+  if (M_out == nullptr) return set_error(DCTF_EINVAL, "M_out must not be NULL");
   if ((reinterpret_cast<uintptr_t>(M_out) & 15) || (reinterpret_cast<uintptr_t>(H_out) & 15))
     return set_error(DCTF_EINVAL, "M_out and H_out must be 16-byte aligned");
-  if (mh < 1 || mw < 1 || mh > n || mw > n)
-    return set_error(DCTF_EINVAL, "mask %dx%d must fit in the %dx%d block", mh, mw, n, n);
-  if (anchor[0] < 0 || anchor[0] >= mh || anchor[1] < 0 || anchor[1] >= mw)
-    return set_error(DCTF_EINVAL, "anchor (%d,%d) outside the %dx%d mask", anchor[0], anchor[1],
-                     mh, mw);
-  if (boundary != DCTF_ZERO && boundary != DCTF_REPLICATE)
-    return set_error(DCTF_EINVAL, "boundary %d: must be DCTF_ZERO or DCTF_REPLICATE", boundary);
-  MaskParams mp;
-  memset(&mp, 0, sizeof mp);
-  for (int k = 0; k < mh * mw; ++k) {
-    if (!isfinite(mask[k])) return set_error(DCTF_EINVAL, "mask entry %d is not finite", k);
-    mp.w[k] = mask[k];
-  }
-  mp.mh = mh; mp.mw = mw; mp.ar = anchor[0]; mp.ac = anchor[1]; mp.n = n; mp.boundary = boundary;
   double *scratch = nullptr;
   cudaError_t e = scratch_on_current_device(&scratch);
-  if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static build scratch)");
+  if (e != cudaSuccess) return cuda_error(e, "device address of the static build scratch");
   double *G = scratch;                                  // first half
   double *H = H_out != nullptr ? H_out : scratch + n2 * n2;
   build_hg_noalloc_kernel<<<(unsigned)n2, (unsigned)n2, 0, stream>>>(mp, H, G);

@@ -88,8 +88,8 @@ void *mapped_host(const void *p, size_t bytes) {
   return a.devicePointer;
 }
 
-static dctf_status check_mask(const double *mask, int mh, int mw, const int anchor[2],
-                              int n, int boundary, MaskParams *mp) {
+dctf_status check_mask(const double *mask, int mh, int mw, const int anchor[2], int n,
+                       int boundary, MaskParams *mp) {
   if (n != 4 && n != 8 && n != 16)
     return set_error(DCTF_EINVAL, "block size n=%d: must be 4, 8 or 16", n);
   if (mask == nullptr || anchor == nullptr)
@@ -130,7 +130,7 @@ using namespace dctf;
 
 extern "C" {
 
-int dctf_version(void) { return 300; }   // 0.3.0
+int dctf_version(void) { return 400; }   // 0.4.0
 
 const char *dctf_last_error(void) { return g_last_error.c_str(); }
 

@@ -34,6 +34,12 @@ struct MaskParams {
   int mh, mw, ar, ac, n, boundary;
 };
 
+// Argument checks shared by every entry point that takes a mask (capi.cu):
+// n in {4, 8, 16}, non-NULL mask and anchor, 1 <= mh, mw <= n, anchor inside
+// the mask, a known boundary, finite entries.  Fills *mp; EINVAL otherwise.
+dctf_status check_mask(const double *mask, int mh, int mw, const int anchor[2], int n,
+                       int boundary, MaskParams *mp);
+
 // Byte layout of the tensor-core B operand ("pieces"): for every 64-element
 // chunk kc of the input index k, R stacked rows of 128 bytes (64 fp16/bf16,
 // or 32 fp32), 16-byte units XOR-swizzled by (row & 7), i.e. the canonical

@@ -1,7 +1,7 @@
 // Continuous-batching server for quantised (int16) block-DCT planes.
 //
-// Requests (1-4 int16 coefficient planes, one quantisation table per plane,
-// one mask) arrive from any thread.  One worker thread:
+// Requests (1-4 int16 coefficient planes, a dequantisation and a
+// requantisation table per plane, one mask) arrive from any thread.  One worker thread:
 //   * retires finished batches (CUDA event per batch): copies results to the
 //     caller's buffers, frees their share of the HBM budget, records latency;
 //   * admits waiting requests, in arrival order, while a batch slot is free
@@ -134,7 +134,8 @@ struct Req {
   const int16_t *in[kMaxPlanes] = {};
   int16_t *out[kMaxPlanes] = {};
   int64_t nblocks[kMaxPlanes] = {};
-  uint16_t q[kMaxPlanes][64] = {};
+  uint16_t q[kMaxPlanes][64] = {};      // dequantisation table per plane
+  uint16_t qout[kMaxPlanes][64] = {};   // requantisation table per plane
   OpKey key;
   double t_submit = 0, t_done = 0;
   // arena layout: [inputs][outputs], each plane 256-aligned (host-direct
@@ -149,6 +150,7 @@ struct Req {
   bool in_pinned = false;    // caller buffers already page-locked: copied by DMA directly
   bool out_pinned = false;
   bool direct = false;       // every plane mapped page-locked: the kernel does the I/O
+  bool waited = false;       // did not fit the HBM budget at the head of the queue
 };
 
 // Page-locked (or registered) host memory can be the source / target of an
@@ -192,7 +194,8 @@ bool direct_planes(Req *r) {
 }
 
 // Per-batch upload buffer (pinned on the host, mirrored on the device):
-// [GroupItem x nitems][q table x nitems][status word], packed per batch.
+// [GroupItem x nitems][(q_in, q_out) tables x nitems][status word], packed
+// per batch.
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
@@ -228,7 +231,8 @@ struct dctf_server {
   // statistics (under mu)
   std::vector<double> lat_ms;
   uint64_t completed = 0, failed = 0, batches = 0, blocks = 0, hits = 0, misses = 0, builds = 0;
-  uint64_t direct = 0;
+  uint64_t direct = 0, budget_waits = 0;
+  size_t hbm_peak = 0;
   double t_first_submit = 0, t_last_done = 0;
   int max_batch_seen = 0;
 };
@@ -340,7 +344,7 @@ dctf_status launch_batch(dctf_server *s, Slot &sl, std::vector<Req *> &batch) {
   }
   char *hb = reinterpret_cast<char *>(sl.h_items), *db = reinterpret_cast<char *>(sl.d_items);
   const size_t q0 = (size_t)nitems * sizeof(GroupItem);
-  const size_t err_off = q0 + (size_t)nitems * kQBytes;
+  const size_t err_off = q0 + (size_t)nitems * 2 * kQBytes;
   uint32_t *d_err = reinterpret_cast<uint32_t *>(db + err_off);
   int id = 0, is = ndirect;
   int64_t hd = 0, hs = 0;
@@ -364,15 +368,17 @@ dctf_status launch_batch(dctf_server *s, Slot &sl, std::vector<Req *> &batch) {
     for (int p = 0; p < r->nplanes; ++p) {
       const int i = r->direct ? id++ : is++;
       GroupItem &gi = sl.h_items[i];
-      memcpy(hb + q0 + (size_t)i * kQBytes, r->q[p], kQBytes);
-      const uint16_t *dq = reinterpret_cast<const uint16_t *>(db + q0 + (size_t)i * kQBytes);
+      memcpy(hb + q0 + (size_t)(2 * i) * kQBytes, r->q[p], kQBytes);
+      memcpy(hb + q0 + (size_t)(2 * i + 1) * kQBytes, r->qout[p], kQBytes);
+      const uint16_t *dq = reinterpret_cast<const uint16_t *>(db + q0 + (size_t)(2 * i) * kQBytes);
+      const uint16_t *dqo = dq + 64;
       if (r->direct) {
-        e = fill_group_item_host(&gi, r->op->op, r->din[p], r->dout[p], r->nblocks[p], dq, dq);
+        e = fill_group_item_host(&gi, r->op->op, r->din[p], r->dout[p], r->nblocks[p], dq, dqo);
         gi.half_begin = hd;
         hd += (r->nblocks[p] + 63) / 64;
       } else {
         e = fill_group_item(&gi, r->op->op, s->d_arena + r->in_off[p], s->d_arena + r->out_off[p],
-                            r->nblocks[p], true, dq, dq);
+                            r->nblocks[p], true, dq, dqo);
         gi.half_begin = hs;
         hs += (r->nblocks[p] + 63) / 64;
       }
@@ -432,7 +438,11 @@ void worker_loop(dctf_server *s) {
         while (!s->pending.empty() && (int)batch.size() < s->cfg.max_batch_requests) {
           Req *r = s->pending.front();
           if (planes + r->nplanes > free_slot->cap) break;
-          if (r->bytes > 0 && !s->arena.alloc(r->bytes, &r->off)) break;   // wait for memory
+          if (r->bytes > 0 && !s->arena.alloc(r->bytes, &r->off)) {   // wait for memory
+            if (!r->waited) { r->waited = true; ++s->budget_waits; }
+            break;
+          }
+          s->hbm_peak = std::max(s->hbm_peak, s->arena.used());
           s->pending.pop_front();
           planes += r->nplanes;
           batch.push_back(r);
@@ -507,7 +517,7 @@ dctf_status dctf_server_create(const dctf_server_cfg *cfg, dctf_server **out) {
     sl.cap = cap;
     e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-    const size_t ub = (size_t)cap * (sizeof(GroupItem) + kQBytes) + 256;
+    const size_t ub = (size_t)cap * (sizeof(GroupItem) + 2 * kQBytes) + 256;
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_items, ub, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_err, 64, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&sl.d_items, ub);
@@ -543,12 +553,13 @@ dctf_status dctf_server_submit(dctf_server *s, const dctf_request *rq, uint64_t 
     r->out[p] = rq->out[p];
     r->nblocks[p] = rq->nblocks[p];
     memcpy(r->q[p], rq->q[p], 128);
+    memcpy(r->qout[p], rq->q_out[p] != nullptr ? rq->q_out[p] : rq->q[p], 128);
   }
   r->key.w.assign(rq->mask, rq->mask + rq->mh * rq->mw);
   r->key.mh = rq->mh; r->key.mw = rq->mw;
   r->key.ar = rq->anchor[0]; r->key.ac = rq->anchor[1];
   r->key.boundary = rq->boundary;
-  r->direct = direct_planes(r);
+  r->direct = !s->cfg.staged_only && direct_planes(r);
   r->bytes = r->direct ? 0 : request_bytes(rq);
   if (r->bytes > s->cfg.hbm_budget_bytes) {
     const size_t b = r->bytes;
@@ -616,6 +627,8 @@ dctf_status dctf_server_stats(dctf_server *s, dctf_stats *out) {
   out->wall_s = s->t_last_done > s->t_first_submit ? (s->t_last_done - s->t_first_submit) / 1e3 : 0;
   out->hbm_in_use = s->arena.used();
   out->direct_requests = s->direct;
+  out->budget_waits = s->budget_waits;
+  out->hbm_peak = s->hbm_peak;
   return DCTF_OK;
 }
 

@@ -57,7 +57,7 @@ def test_headers_compile_standalone(lang, tmp_path):
 
 
 def test_version(so):
-    assert lib.version() >= 300      # 0.3: host-direct server route (dctf_stats.direct_requests)
+    assert lib.version() >= 400      # 0.4: per-plane output tables, staged_only, admission stats
 
 
 def build(mask, mh, mw, anchor, n, boundary):
@@ -97,3 +97,40 @@ def test_apply_rejects_null_operator(so):
     assert so.dctf_host_buffer_direct(None, 16) == 0
     assert so.dctf_operator_set_precision(None, 0) == 1
     so.dctf_release_operator(None)        # no-op
+
+
+# C struct name -> (ctypes mirror, C field name for each ctypes field)
+_STRUCTS = {
+    "dctf_group_item": (lib._GroupItem, {"inp": "in"}),
+    "dctf_pixel_item": (lib._PixelItem, {}),
+    "dctf_server_cfg": (lib._ServerCfg, {}),
+    "dctf_request": (lib._Request, {"inp": "in"}),
+    "dctf_stats": (lib._Stats, {}),
+}
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structs have the size and field offsets the C
+    header gives them (compiled and printed by the host compiler)."""
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dctf.h"', 'int main(void) {']
+    for cname, (ct, rename) in _STRUCTS.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in ct._fields_:
+            cf = rename.get(f, f)
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, cf))
+    lines.append('return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for ln in filter(None, got):
+        cname, field, value = ln.split()
+        ct = _STRUCTS[cname][0]
+        want = ctypes.sizeof(ct) if field == "size" else getattr(ct, field).offset
+        assert int(value) == want, (cname, field, int(value), want)

@@ -256,20 +256,16 @@ def headline_full():
     return job, blocks, x.astype(np.float32)
 
 
-def test_full_size_headline_sampled(dctf, headline_full):
-    """The full 4096x4096 workload in the benchmark's launch configuration;
-    the oracle checks a sample of blocks (first and last tile, random rest),
-    and the two kernels agree on every block."""
+def test_full_size_headline_every_block(dctf, headline_full):
+    """The full 4096x4096 workload in the benchmark's launch configuration:
+    every block of both kernels against the oracle (coefficients and uint8
+    pixels of the spatial filter), and the two kernels agree."""
     job, blocks, x = headline_full
     op = dctf.build_operator(job.mask, job.anchor, 8, job.boundary)
     y_tc = run(dctf, op, x, dctf.F16X3)
     y_simt = run(dctf, op, x, dctf.FP32_SIMT)
-    nb = x.shape[0]
-    g = np.random.default_rng(95)
-    idx = np.unique(np.concatenate([np.arange(128), np.arange(nb - 128, nb),
-                                    g.integers(0, nb, 4096)]))
     for y in (y_tc, y_simt):
-        check(y[idx], x[idx], blocks[idx], job.mask, job.anchor, 8, job.boundary)
+        check(y, x, blocks, job.mask, job.anchor, 8, job.boundary)
     assert np.abs(y_tc - y_simt).max() <= 2 * COEF_TOL
     assert op.status() == 0
 

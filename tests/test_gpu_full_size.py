@@ -1,6 +1,7 @@
 """GPU: the full-size workloads in the launch configurations the benchmark
-times, checked against the oracle on sampled blocks (the oracle computes each
-sampled block's output on its own) and by properties that hold at any size.
+times, checked against the oracle on EVERY block (the oracle's apply and its
+spatial filter are vectorised FP64 passes) and by properties that hold at
+any size.
 
 * the grouped workload: 64 images of seeded sizes (~870k blocks), each with
   its own operator, in one persistent launch after autotuning;
@@ -26,6 +27,10 @@ COEF_TOL = 1e-3
 BAND = 1e-4
 
 
+def _pinned_sample(nb):
+    return np.unique(np.linspace(0, nb - 1, 257).astype(int))
+
+
 def dct_full(blocks):
     """C X C^T for every block as two FP64 GEMMs (the oracle's einsum is
     too slow for 262,144 16 x 16 blocks); pinned to oracle.dct2_blocks on a
@@ -35,25 +40,33 @@ def dct_full(blocks):
     t = (blocks.reshape(-1, n) @ c.T).reshape(nb, n, n)              # X C^T
     out = (t.transpose(0, 2, 1).reshape(-1, n) @ c.T).reshape(nb, n, n).transpose(0, 2, 1)
     x = np.ascontiguousarray(out).reshape(nb, n * n)
-    idx = np.linspace(0, nb - 1, 257).astype(int)
+    idx = _pinned_sample(nb)
     assert np.abs(x[idx] - oracle.dct2_blocks(blocks[idx])).max() < 1e-9
     return x
 
 
-def sample_index(nb, seed, tile=128, k=4096):
-    g = np.random.default_rng(seed)
-    return np.unique(np.concatenate([np.arange(min(nb, tile)), np.arange(max(0, nb - tile), nb),
-                                     g.integers(0, nb, k)]))
+def idct_full(y, n):
+    """C^T Y C for every block as two FP64 GEMMs; pinned to
+    oracle.idct2_blocks on a sample before use.  [nb, n, n]."""
+    y = np.asarray(y, dtype=np.float64).reshape(-1, n, n)
+    nb = y.shape[0]
+    c = oracle.dct_matrix(n)
+    t = (y.reshape(-1, n) @ c).reshape(nb, n, n)                     # Y C
+    out = (t.transpose(0, 2, 1).reshape(-1, n) @ c).reshape(nb, n, n).transpose(0, 2, 1)
+    out = np.ascontiguousarray(out)
+    idx = _pinned_sample(nb)
+    assert np.abs(out[idx] - oracle.idct2_blocks(y[idx].reshape(-1, n * n), n)).max() < 1e-9
+    return out
 
 
-def check_sample(y, x32, blocks, w, a, n, boundary, bound=None):
-    m = oracle.build_M(w, a, n, boundary)
+def check_all(y, x32, p_sp, m, n, bound=None):
+    """Every block: coefficients against the oracle's y = M x in FP64, and
+    (exact arithmetics) uint8 pixels against the oracle's spatial filter."""
     y_ref = oracle.apply_M(m, x32.astype(np.float64))
     err = np.abs(y - y_ref)
     if bound is None:
         assert err.max() <= COEF_TOL, err.max()
-        p_sp = oracle.spatial_filter_blocks(blocks, w, a, boundary)
-        st = oracle.uint8_compare(p_sp, oracle.to_uint8(oracle.idct2_blocks(y, n)), BAND)
+        st = oracle.uint8_compare(p_sp, oracle.to_uint8(idct_full(y, n)), BAND)
         assert st["mismatch"] == 0, st
     else:
         assert (err <= bound(m, x32.astype(np.float64))).all()
@@ -66,7 +79,8 @@ def grouped_full():
     data = []
     for job in jobs:
         blocks = oracle.image_to_blocks(job.image, 8)
-        data.append((job, blocks, dct_full(blocks).astype(np.float32)))
+        p_sp = oracle.spatial_filter_blocks(blocks, job.mask, job.anchor, job.boundary)
+        data.append((job, p_sp, dct_full(blocks).astype(np.float32)))
     return data
 
 
@@ -82,12 +96,11 @@ def test_grouped_full_workload(dctf, grouped_full):
     g.launch()
     torch.cuda.synchronize()
     assert g.status() == 0
-    for i, ((op, xd, yd, nb), (job, blocks, x)) in enumerate(zip(items, grouped_full)):
+    for (op, xd, yd, nb), (job, p_sp, x) in zip(items, grouped_full):
         y = yd.cpu().numpy()
         assert np.isfinite(y).all()                        # every block written
-        idx = sample_index(nb, i, k=256)
-        check_sample(y[idx].astype(np.float64), x[idx], blocks[idx], job.mask, job.anchor, 8,
-                     job.boundary)
+        check_all(y.astype(np.float64), x, p_sp, oracle.build_M(job.mask, job.anchor, 8,
+                                                                  job.boundary), 8)
         y1 = torch.empty_like(xd)
         dctf.apply(op, xd, nb, y1)                         # one plain launch: the same bits
         torch.cuda.synchronize()
@@ -101,13 +114,15 @@ def test_grouped_full_workload(dctf, grouped_full):
 def large_full():
     job = datagen.large_job()
     blocks = oracle.image_to_blocks(job.image, 16)
-    return job, blocks, dct_full(blocks).astype(np.float32)
+    x = dct_full(blocks).astype(np.float32)
+    p_sp = oracle.spatial_filter_blocks(blocks, job.mask, job.anchor, job.boundary)
+    return job, p_sp, x, oracle.build_M(job.mask, job.anchor, 16, job.boundary)
 
 
 @pytest.mark.parametrize("prec", ["F16X3", "BF16X6", "TF32X3", "FP32_SIMT", "BF16X3", "TF32X1",
                                   "KRON_FP32"])
 def test_large_16x16_full_workload(dctf, large_full, prec):
-    job, blocks, x = large_full
+    job, p_sp, x, m = large_full
     nb = x.shape[0]
     assert nb == 262144
     op = dctf.build_operator(job.mask, job.anchor, 16, job.boundary, kron=(prec == "KRON_FP32"))
@@ -119,10 +134,8 @@ def test_large_16x16_full_workload(dctf, large_full, prec):
     assert op.status() == 0
     y = yd.cpu().numpy()
     assert np.isfinite(y).all()
-    idx = sample_index(nb, 16)
     bound = {"BF16X3": bf16x3_bound, "TF32X1": tf32x1_bound}.get(prec)
-    check_sample(y[idx].astype(np.float64), x[idx], blocks[idx], job.mask, job.anchor, 16,
-                 job.boundary, bound)
+    check_all(y.astype(np.float64), x, p_sp, m, 16, bound)
     op.release()
 
 
@@ -130,22 +143,22 @@ def test_large_16x16_full_workload(dctf, large_full, prec):
 def headline_full():
     job = datagen.headline_job()
     blocks = oracle.image_to_blocks(job.image, 8)
-    return job, blocks, dct_full(blocks).astype(np.float32)
+    p_sp = oracle.spatial_filter_blocks(blocks, job.mask, job.anchor, job.boundary)
+    return job, p_sp, dct_full(blocks).astype(np.float32)
 
 
 def test_pixels_and_planar_full_workload(dctf, headline_full):
-    job, blocks, x = headline_full
+    job, p_sp, x = headline_full
     h, w = job.image.shape
+    m = oracle.build_M(job.mask, job.anchor, 8, job.boundary)
     op = dctf.build_operator(job.mask, job.anchor, 8, job.boundary)
     xd = torch.from_numpy(x).cuda()
-    # fused pixel output: uint8 of the spatial filter on sampled blocks
+    # fused pixel output: uint8 of the spatial filter on every block
     img = torch.full((h, w), 77, dtype=torch.uint8, device="cuda")
     dctf.apply_pixels(op, xd, h, w, img)
     torch.cuda.synchronize()
     got = oracle.image_to_blocks(img.cpu().numpy(), 8)
-    idx = sample_index(x.shape[0], 8)
-    p_sp = oracle.spatial_filter_blocks(blocks[idx], job.mask, job.anchor, job.boundary)
-    st = oracle.uint8_compare(p_sp, got[idx], BAND)
+    st = oracle.uint8_compare(p_sp, got, BAND)
     assert st["mismatch"] == 0, st
     # image-plane layout: the same bits as the block-major apply, everywhere
     yb = torch.empty_like(xd)
@@ -157,6 +170,5 @@ def test_pixels_and_planar_full_workload(dctf, headline_full):
     assert op.status() == 0
     got = oracle.image_to_blocks(out.cpu().numpy(), 8).reshape(-1, 64)
     assert np.array_equal(got, yb.cpu().numpy())
-    check_sample(got[idx].astype(np.float64), x[idx], blocks[idx], job.mask, job.anchor, 8,
-                 job.boundary)
+    check_all(got.astype(np.float64), x, p_sp, m, 8)
     op.release()

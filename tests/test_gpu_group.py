@@ -141,8 +141,9 @@ def quantised_plane(img, s):
 
 
 def test_group_int16_dequant_requant(dctf):
-    """JPEG-style int16 planes, each with its own mask and quantisation
-    table: dequantise, filter, requantise in one pass."""
+    """JPEG-style int16 planes, each with its own mask, input table and a
+    different output table: dequantise with q_in, filter, requantise with
+    q_out in one pass (swapping the tables changes the result)."""
     planes = []
     for j in range(6):
         img = datagen.synthetic_image(128 + 64 * (j % 3), 192, datagen.rng(98, j, 0))
@@ -150,20 +151,27 @@ def test_group_int16_dequant_requant(dctf):
         w, a, bnd = datagen.serving_mask(j)
         planes.append((img, s, w, a, bnd))
     items, refs, keep = [], [], []
-    for img, s, w, a, bnd in planes:
+    for j, (img, s, w, a, bnd) in enumerate(planes):
         qin, q = quantised_plane(img, s)
         op = dctf.build_operator(w, a, 8, bnd)
         xd = torch.from_numpy(qin).cuda()
         yd = torch.zeros_like(xd)
+        qo = datagen.quant_table([4, 1, 2][j % 3])       # another scale than q's
         qd = torch.from_numpy(q.ravel().astype(np.int16).view(np.int16)).cuda()
-        keep.append(qd)
-        items.append((op, xd, yd, qin.shape[0], qd, qd))
-        refs.append((qin, q, w, a, bnd))
+        qod = torch.from_numpy(qo.ravel().astype(np.int16).view(np.int16)).cuda()
+        keep += [qd, qod]
+        items.append((op, xd, yd, qin.shape[0], qd, qod))
+        refs.append((qin, q, qo, w, a, bnd))
     g = dctf.group_create(items, io=dctf.IO_I16)
     g.launch()
     torch.cuda.synchronize()
     assert g.status() == 0
-    for (op, xd, yd, nb, _, _), (qin, q, w, a, bnd) in zip(items, refs):
-        out_ref, v = oracle.serve_blocks(qin, q, oracle.build_M(w, a, 8, bnd), q)
-        st = oracle.int16_compare(v, yd.cpu().numpy(), BAND)
+    for (op, xd, yd, nb, _, _), (qin, q, qo, w, a, bnd) in zip(items, refs):
+        m = oracle.build_M(w, a, 8, bnd)
+        _, v = oracle.serve_blocks(qin, q, m, qo)
+        got = yd.cpu().numpy()
+        st = oracle.int16_compare(v, got, BAND)
         assert st["mismatch"] == 0, st
+        # the tables are not interchangeable: the swapped order disagrees
+        _, v_swapped = oracle.serve_blocks(qin, qo, m, q)
+        assert oracle.int16_compare(v_swapped, got, BAND)["mismatch"] > 0

@@ -197,3 +197,64 @@ def test_direct_in_place_overlap_and_budget(dctf, requests):
     assert st["failed"] == 0 and st["direct_requests"] == 2 and st["hbm_in_use"] == 0
     srv.close()
     ref.close()
+
+
+def test_distinct_output_table_both_routes(dctf, requests):
+    """Each plane requantised with its own output table (q_out != q): the
+    host-direct and the staged route give the same bits, equal to the
+    oracle's dequantise-with-q, requantise-with-q_out result."""
+    srv = dctf.Server(hbm_budget_bytes=64 << 20, max_inflight=2, max_batch_requests=4)
+    for j, (planes, w, a, bnd) in enumerate(requests[:4]):
+        qouts = [datagen.quant_table([4, 1, 2][(j + p) % 3]).ravel() for p in range(len(planes))]
+        pin_in = [torch.from_numpy(p[0]).pin_memory() for p in planes]
+        pin_out = [torch.zeros_like(t).pin_memory() for t in pin_in]
+        outs = [np.zeros_like(p[0]) for p in planes]
+        t1 = srv.submit([t.numpy() for t in pin_in], [t.numpy() for t in pin_out],
+                        [p[1] for p in planes], w, a, bnd, qtabs_out=qouts)
+        t2 = srv.submit([p[0] for p in planes], outs, [p[1] for p in planes], w, a, bnd,
+                        qtabs_out=qouts)
+        srv.wait(t1)
+        srv.wait(t2)
+        m = oracle.build_M(w, a, 8, bnd)
+        for (qin, q), qo, tp, o in zip(planes, qouts, pin_out, outs):
+            assert np.array_equal(tp.numpy(), o)
+            _, v = oracle.serve_blocks(qin, q, m, qo)
+            assert oracle.int16_compare(v, o, BAND)["mismatch"] == 0
+            if not np.array_equal(q, qo):
+                _, vs = oracle.serve_blocks(qin, qo, m, q)
+                assert oracle.int16_compare(vs, o, BAND)["mismatch"] > 0
+    st = srv.stats()
+    assert st["failed"] == 0 and st["direct_requests"] == 4
+    srv.close()
+
+
+def test_admission_waits_for_budget(dctf):
+    """A staged_only server with a 1 MiB HBM budget: each request needs
+    0.77 MiB (in + out), so only one fits at a time and the others are
+    admitted as earlier ones complete.  Every result is correct, the server
+    counts the waits, and the budget is never exceeded."""
+    budget = 1 << 20
+    srv = dctf.Server(hbm_budget_bytes=budget, max_inflight=4, max_batch_requests=4,
+                      staged_only=True)
+    g = np.random.default_rng(21)
+    w, a, bnd = datagen.serving_mask(3)
+    m = oracle.build_M(w, a, 8, bnd)
+    q, qo = datagen.quant_table(2).ravel(), datagen.quant_table(1).ravel()
+    reqs = []
+    for k in range(5):
+        x = g.integers(-400, 400, (3072, 64)).astype(np.int16)     # 384 KiB a plane
+        xin = torch.from_numpy(x).pin_memory()                      # page-locked, yet staged
+        xout = torch.zeros_like(xin).pin_memory()
+        reqs.append((x, xin, xout))
+    tickets = [srv.submit([xin.numpy()], [xout.numpy()], [q], w, a, bnd, qtabs_out=[qo])
+               for _, xin, xout in reqs]
+    for t in tickets:
+        srv.wait(t)
+    for x, _, xout in reqs:
+        _, v = oracle.serve_blocks(x, q, m, qo)
+        assert oracle.int16_compare(v, xout.numpy(), BAND)["mismatch"] == 0
+    st = srv.stats()
+    assert st["failed"] == 0 and st["completed"] == 5 and st["direct_requests"] == 0
+    assert st["budget_waits"] >= 1
+    assert 0 < st["hbm_peak"] <= budget and st["hbm_in_use"] == 0
+    srv.close()

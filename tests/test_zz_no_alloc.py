@@ -6,8 +6,8 @@ cudaMalloc's device synchronisation): the caller passes the output buffers
 and the build's scratch is a static array inside the library.  This test
 calls it through the C ABI twice in a row (different masks, block sizes and
 boundaries, so a stale scratch would show) and compares each result with
-dctf_build_operator's, within the builder tests' tolerance.  The file is
-named to be collected last.
+dctf_build_operator's and with the FP64 oracle's M, within the builder
+tests' tolerance.  The file is named to be collected last.
 """
 import ctypes
 
@@ -47,11 +47,15 @@ def test_noalloc_build_matches_allocating_build(dctf):
         op.release()
         scale = max(1.0, np.abs(w).sum())
         assert np.abs(m - m_ref).max() <= 1e-12 * scale
+        assert np.abs(m - oracle.build_M(w, anchor, n, boundary)).max() <= 1e-12 * scale
         if want_h:
             assert np.array_equal(h, h_ref)
-    # beyond the static scratch / invalid block size: rejected before any launch
+            assert np.array_equal(h, oracle.build_H(w, anchor, n, boundary))
+    # a block side beyond the static scratch (2 n^4 doubles > 1 MiB at n = 32):
+    # rejected before any launch, with the scratch limit in the message
     wm = np.ones((3, 3))
     a = (ctypes.c_int * 2)(1, 1)
     buf = torch.empty(1024, dtype=torch.float64, device="cuda")
     assert so.dctf_build_matrix_noalloc(wm.ctypes.data, 3, 3, ctypes.addressof(a), 32, 0,
                                         buf.data_ptr(), None, None) == 1
+    assert "scratch" in dctf.last_error()
