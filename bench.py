@@ -513,7 +513,8 @@ def run_workloads(lib, torch, reps: int):
     # (Eq. 3) of each block's coefficient error, C^T E C
     u = np.arange(16)[:, None]
     c16 = np.sqrt(np.where(u == 0, 1.0, 2.0) / 16) * np.cos(np.pi * (2 * np.arange(16)[None, :] + 1) * u / 32)
-    for name in ("F16X3", "BF16X6", "BF16X3", "TF32X3", "TF32X1", "FP32_SIMT", "KRON_FP32"):
+    for name in ("F16X3", "BF16X6", "BF16X3", "TF32X3", "TF32X1", "FP32_SIMT", "KRON_FP32",
+                 "KRON_F16X3"):
         op.set_precision(getattr(lib, name))
         t = graph_time_ms(torch, lambda s: lib.apply(op, xl, nb, yl, stream=s), max(1, reps // 4))
         e = yl[idx.to(dev)].double().cpu().numpy() - ys64
@@ -521,7 +522,7 @@ def run_workloads(lib, torch, reps: int):
         res[name] = {"us": 1e3 * t, "blocks_per_s": nb / (t / 1e3),
                      "GBps": nb * 2048 / (t / 1e3) / 1e9,
                      "max_coef_err_vs_fp64": float(np.abs(e).max()), "max_pixel_err_vs_fp64": perr}
-    res["KRON_FP32"]["terms"] = op.kron_rank()
+    res["KRON_FP32"]["terms"] = res["KRON_F16X3"]["terms"] = op.kron_rank()
     op.release()
     # the paper form's best case: a separable mask (the workload's 9x9
     # Gaussian without its perturbation, one Kronecker term)
@@ -529,7 +530,7 @@ def run_workloads(lib, torch, reps: int):
     op = lib.build_operator(sep, job.anchor, 16, job.boundary, kron=True)
     m64, _ = op.download()
     ys64 = xl[idx.to(dev)].double().cpu().numpy() @ m64.T
-    for name in ("KRON_FP32", "F16X3"):
+    for name in ("KRON_FP32", "KRON_F16X3", "F16X3"):
         op.set_precision(getattr(lib, name))
         t = graph_time_ms(torch, lambda s: lib.apply(op, xl, nb, yl, stream=s), max(1, reps // 4))
         e = yl[idx.to(dev)].double().cpu().numpy() - ys64
@@ -538,7 +539,7 @@ def run_workloads(lib, torch, reps: int):
                                         "max_coef_err_vs_fp64": float(np.abs(e).max()),
                                         "max_pixel_err_vs_fp64": float(np.abs(
                                             c16.T @ e.reshape(-1, 16, 16) @ c16).max())}
-    res["separable_9x9_KRON_FP32"]["terms"] = op.kron_rank()
+    res["separable_9x9_KRON_FP32"]["terms"] = res["separable_9x9_KRON_F16X3"]["terms"] = op.kron_rank()
     out["large_8192x8192_16x16"] = res
     op.release()
     return out

@@ -86,7 +86,12 @@ typedef enum { DCTF_ZERO = 0, DCTF_REPLICATE = 1 } dctf_boundary;
  *              on CUDA cores; r * 2 n^3 multiply-adds per block instead of
  *              n^4 (8x fewer for a separable mask at n = 16).  Needs an
  *              operator built with DCTF_BUILD_KRON; n = 4, 8, 16.
- * The tensor-core variants of 16x16 blocks do not run in place.
+ *  KRON_F16X3: the same sandwich products on tcgen05 tensor cores with the
+ *              F16X3 split (Sec. II.B Eq. 11-12, Sec. II.C Eq. 20): per
+ *              term, Z_t = X B_t^T, then Y = sum_t A_t Z_t, both FP16 hi/lo
+ *              products accumulated in FP32, Z re-split between the two;
+ *              |x| must stay below 65504.  n = 16; runs in place.
+ * The dense tensor-core variants of 16x16 blocks do not run in place.
  * dctf_operator_set_precision returns DCTF_EUNSUPPORTED for a variant that
  * has no kernel for the operator's n. */
 typedef enum {
@@ -96,7 +101,8 @@ typedef enum {
     DCTF_TF32X1 = 3,
     DCTF_TF32X3 = 4,
     DCTF_KRON_FP32 = 5,
-    DCTF_BF16X3 = 6
+    DCTF_BF16X3 = 6,
+    DCTF_KRON_F16X3 = 7
 } dctf_precision;
 
 typedef struct dctf_operator dctf_operator;
@@ -121,10 +127,12 @@ dctf_status dctf_build_operator(const double *mask, int mh, int mw,
  * rotated by 180 degrees and the anchor mirrored to (mh-1-ar, mw-1-ac). */
 enum { DCTF_MASK_CONVOLUTION = 1u };
 /* DCTF_BUILD_KRON: also keep the operator's Kronecker factors (every
- * rebuild recomputes them): the host splits the mask into rank(w) separable
- * terms by Gaussian elimination with complete pivoting (terms below 1e-13 of
- * the largest entry are dropped), and the device forms the DCT-domain 1-D
- * filters of each term in FP64 (stored FP32).  Enables DCTF_KRON_FP32. */
+ * rebuild recomputes them, all on the device in FP64): the mask is split
+ * into rank(w) separable terms by Gaussian elimination with complete
+ * pivoting (terms below 1e-13 of the largest entry are dropped), and the
+ * DCT-domain 1-D filters of each term are formed (kept in FP64 and FP32;
+ * for n = 16 also as FP16 tensor-core pieces).  Enables DCTF_KRON_FP32 and,
+ * for n = 16, DCTF_KRON_F16X3. */
 enum { DCTF_BUILD_KRON = 2u };
 dctf_status dctf_build_operator_ex(const double *mask, int mh, int mw,
                                    const int anchor[2], int n,
@@ -171,8 +179,9 @@ dctf_status dctf_operator_download(const dctf_operator *op, double *M_host,
 dctf_status dctf_operator_status(dctf_operator *op, uint32_t *code, int clear);
 
 /* Number of Kronecker terms of an operator built with DCTF_BUILD_KRON (the
- * numerical rank of its mask; 0 for an all-zero mask).  EUNSUPPORTED for an
- * operator built without the flag.  Host only, no synchronisation. */
+ * numerical rank of its mask; 0 for an all-zero mask), as the device build
+ * found it: synchronises the device and reads it back.  EUNSUPPORTED for an
+ * operator built without the flag. */
 dctf_status dctf_operator_kron_rank(const dctf_operator *op, int *rank);
 
 void dctf_release_operator(dctf_operator *op);

@@ -15,6 +15,7 @@ import numpy as np
 
 __all__ = [
     "ZERO", "REPLICATE", "FP32_SIMT", "F16X3", "BF16X6", "TF32X1", "TF32X3", "KRON_FP32", "BF16X3",
+    "KRON_F16X3",
     "DctfError", "load", "lib_path", "exported_symbols", "build_operator", "Operator",
     "apply", "apply_f64in", "apply_host", "host_buffer_direct", "apply_pixels", "apply_planar", "forward_dct", "forward_dct_i16", "inverse_dct_u8", "last_error",
     "version", "IO_F32", "IO_I16", "Group", "group_create", "group_create_pixels", "apply_grouped",
@@ -25,7 +26,7 @@ ZERO, REPLICATE = 0, 1
 IO_F32, IO_I16 = 0, 1
 APPLY_INPUTS_READY = 1
 MASK_CONVOLUTION, BUILD_KRON = 1, 2
-FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3, KRON_FP32, BF16X3 = 0, 1, 2, 3, 4, 5, 6
+FP32_SIMT, F16X3, BF16X6, TF32X1, TF32X3, KRON_FP32, BF16X3, KRON_F16X3 = 0, 1, 2, 3, 4, 5, 6, 7
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ETIMEOUT",
            6: "EUNSUPPORTED"}
 

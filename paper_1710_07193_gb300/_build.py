@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libdctf.so")
 
-SOURCES = ["capi.cu", "builder.cu", "apply_simt.cu", "apply_group.cu", "apply_n16.cu", "group_api.cu", "server.cu", "pixels.cu", "selftest.cu", "kron.cu"]
+SOURCES = ["capi.cu", "builder.cu", "apply_simt.cu", "apply_group.cu", "apply_n16.cu", "group_api.cu",
+           "server.cu", "pixels.cu", "selftest.cu", "kron.cu", "kron_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

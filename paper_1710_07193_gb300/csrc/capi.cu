@@ -152,7 +152,8 @@ static dctf_status build_operator(const double *mask, int mh, int mw, const int 
   const bool wide = n == 16;                  // BF16 and TF32 pieces too
   const bool pix = n == 8;                    // pixel operator pieces too
   size_t off = 0, o_C64, o_M64, o_H64, o_M32, o_Mdc, o_f16 = 0, o_bf16 = 0, o_tf32 = 0,
-         o_pix = 0, o_gdc = 0, o_kA = 0, o_kB = 0, o_err;
+         o_pix = 0, o_gdc = 0, o_kA = 0, o_kB = 0, o_kA64 = 0, o_kB64 = 0, o_kmisc = 0,
+         o_kpieces = 0, o_err;
   o_C64 = off; off = align_up(off + n2 * 8, 1024);
   o_M64 = off; off = align_up(off + sq * 8, 1024);
   o_H64 = off; off = align_up(off + sq * 8, 1024);
@@ -170,6 +171,10 @@ static dctf_status build_operator(const double *mask, int mh, int mw, const int 
   if (kron) {
     o_kA = off; off = align_up(off + (size_t)kMaxN * n2 * 4, 1024);
     o_kB = off; off = align_up(off + (size_t)kMaxN * n2 * 4, 1024);
+    o_kA64 = off; off = align_up(off + (size_t)kMaxN * n2 * 8, 1024);
+    o_kB64 = off; off = align_up(off + (size_t)kMaxN * n2 * 8, 1024);
+    o_kmisc = off; off = align_up(off + 256, 1024);
+    if (wide) { o_kpieces = off; off = align_up(off + kKronPieceBytes, 1024); }
   }
   o_err = off; off = align_up(off + 256, 1024);
   cudaError_t e = cudaMalloc(&op->d_base, off);
@@ -189,6 +194,11 @@ static dctf_status build_operator(const double *mask, int mh, int mw, const int 
   op->kron = kron;
   op->d_kA = kron ? reinterpret_cast<float *>(b + o_kA) : nullptr;
   op->d_kB = kron ? reinterpret_cast<float *>(b + o_kB) : nullptr;
+  op->d_kA64 = kron ? reinterpret_cast<double *>(b + o_kA64) : nullptr;
+  op->d_kB64 = kron ? reinterpret_cast<double *>(b + o_kB64) : nullptr;
+  op->d_krank = kron ? reinterpret_cast<int *>(b + o_kmisc) : nullptr;
+  op->d_kscale = kron ? reinterpret_cast<float *>(b + o_kmisc + 16) : nullptr;
+  op->d_kpieces = kron && wide ? reinterpret_cast<uint8_t *>(b + o_kpieces) : nullptr;
   op->d_err = reinterpret_cast<uint32_t *>(b + o_err);
   op->precision = pieces ? DCTF_F16X3 : DCTF_FP32_SIMT;
 
@@ -246,10 +256,12 @@ dctf_status dctf_operator_rebuild(dctf_operator *op, const double *mask, int mh,
 dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p) {
   if (op == nullptr) return set_error(DCTF_EINVAL, "operator is NULL");
   if (p == DCTF_FP32_SIMT) { op->precision = p; return DCTF_OK; }
-  if (p == DCTF_KRON_FP32) {
+  if (p == DCTF_KRON_FP32 || p == DCTF_KRON_F16X3) {
     if (!op->kron)
-      return set_error(DCTF_EUNSUPPORTED, "DCTF_KRON_FP32 needs an operator built with "
+      return set_error(DCTF_EUNSUPPORTED, "the Kronecker form needs an operator built with "
                                           "DCTF_BUILD_KRON");
+    if (p == DCTF_KRON_F16X3 && op->n != 16)
+      return set_error(DCTF_EUNSUPPORTED, "DCTF_KRON_F16X3 has a kernel for n=16 only");
     op->precision = p;
     return DCTF_OK;
   }
@@ -271,7 +283,8 @@ dctf_status dctf_operator_set_flags(dctf_operator *op, uint32_t flags) {
 dctf_status dctf_operator_kron_rank(const dctf_operator *op, int *rank) {
   if (op == nullptr || rank == nullptr) return set_error(DCTF_EINVAL, "NULL argument");
   if (!op->kron) return set_error(DCTF_EUNSUPPORTED, "operator built without DCTF_BUILD_KRON");
-  *rank = op->krank;
+  DCTF_CUDA(cudaDeviceSynchronize());     // the rank is found by the device build
+  DCTF_CUDA(cudaMemcpy(rank, op->d_krank, sizeof(int), cudaMemcpyDeviceToHost));
   return DCTF_OK;
 }
 
@@ -334,6 +347,10 @@ static dctf_status apply_impl(const dctf_operator *op, const float *coeffs, int6
   } else if (op->precision == DCTF_KRON_FP32) {
     e = launch_apply_kron(op, coeffs, nblocks, out, stream);   // in place is fine: a thread
                                                                // writes only the row it read
+  } else if (op->precision == DCTF_KRON_F16X3) {
+    e = launch_apply_kron_tc(op, coeffs, nblocks, out, stream);   // in place is fine: a unit of
+                                                                  // 8 blocks is read before its
+                                                                  // output is written
   } else if (op->n == 16) {
     if (static_cast<const void *>(coeffs) == static_cast<const void *>(out))
       return set_error(DCTF_EINVAL,

@@ -77,8 +77,13 @@ struct dctf_operator {
                             //   BF16X3 uses m0, m1)
   uint32_t *d_tf32;         // n = 16: TF32 pieces hi, lo (2 n2 rows per 32-chunk)
   bool kron;                // built with DCTF_BUILD_KRON: Kronecker factors kept
-  int krank;                //   number of terms of M = sum_t A_t kron B_t
+  int krank_bound;          //   min(mh, mw) of the last build: at least the number of terms
+  int *d_krank;             //   device: number of terms of M = sum_t A_t kron B_t
+  float *d_kscale;          //   device, n = 16: [0] 2^(sZ - sB), [1] 2^-(sZ + sA)
   float *d_kA, *d_kB;       //   [kMaxN][n][n] FP32 each (DCT-domain 1-D filters)
+  double *d_kA64, *d_kB64;  //   the same in FP64
+  uint8_t *d_kpieces;       //   n = 16: FP16 hi/lo pieces of B_t (16 KB) and A_t (16 KB)
+                            //   in the tcgen05 B-operand layout (kron_tc.cu)
   uint32_t *d_err;          // device status word
   // dctf_apply_host staging (lazily allocated): kHostPipes streams, each
   // with an input and an output chunk buffer
@@ -111,11 +116,15 @@ inline bool tc_supported(int n, dctf_precision p) {
 cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks,
                              float *y, cudaStream_t s);
 
-// kron.cu: the Kronecker (sandwich-product) form of the operator
-int kron_split_mask(const MaskParams &mp, double (*u)[kMaxN], double (*v)[kMaxN]);
+// kron.cu: the Kronecker (sandwich-product) form of the operator, built on
+// the device (rank split, factors, and for n = 16 the tensor-core pieces)
+constexpr int kKronPieceBytes = 32768;
 cudaError_t launch_kron_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s);
 cudaError_t launch_apply_kron(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
                               cudaStream_t s);
+// kron_tc.cu: the sandwich products on tensor cores (n = 16, F16X3)
+cudaError_t launch_apply_kron_tc(const dctf_operator *op, const float *x, int64_t nblocks,
+                                 float *y, cudaStream_t s);
 
 int sm_count(int device);
 

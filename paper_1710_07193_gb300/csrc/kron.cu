@@ -15,10 +15,14 @@
 // that is r * 2 N^3 multiply-adds instead of N^4: 8x fewer for a separable
 // mask at N = 16, the same as the dense product at r = N / 2.
 //
-// Build: the host splits the mask into rank-1 terms by Gaussian elimination
-// with complete pivoting (exact up to FP64 rounding, stops at the numerical
-// rank); one CTA per (term, side) forms the 1-D filter matrix and its DCT
-// form C H C^T in FP64 and stores it in FP32.
+// Build, all on the device in FP64: one CTA per (term, side).  Every CTA
+// first splits the mask into rank-1 terms by Gaussian elimination with
+// complete pivoting (the same deterministic steps in every CTA, so all agree
+// on the split; exact up to FP64 rounding, stopping at the numerical rank),
+// then, if its term exists, forms the 1-D filter matrix of its side and its
+// DCT form C H C^T, stored in FP64 and FP32; CTA 0 records the rank.  For
+// 16x16 blocks one more CTA then writes the FP16 pieces of every factor for
+// the tensor-core form (kron_tc.cu) and their scales.
 //
 // Apply: 256 threads, thread = (block, rows i and i + N/2).  Per term:
 // U = X B_t^T row by row (the two X rows in registers, B_t from shared
@@ -37,29 +41,83 @@ namespace dctf {
 namespace {
 
 constexpr int kMaxTerms = kMaxN;
+constexpr int kBuildThreads = 256;
 
-struct KronParams {
-  double u[kMaxTerms][kMaxN];   // column factor of term t (mask rows)
-  double v[kMaxTerms][kMaxN];   // row factor of term t (mask columns)
-  int rank, mh, mw, ar, ac, n, boundary;
-};
+// Gaussian elimination with complete pivoting on the mask, by all threads of
+// the CTA: each step takes the largest remaining |R[p][q]| (the first in
+// row-major order among equals) as pivot, emits u = R[:, q] / R[p][q],
+// v = R[p, :] and subtracts u v^T; it stops when the largest remainder is
+// not above 1e-13 of the mask's largest entry (the numerical rank).  Returns
+// the number of terms; u[t][r], v[t][c] in shared memory.
+__device__ int split_mask(const MaskParams &mp, double (*R)[kMaxN], double (*u)[kMaxN],
+                          double (*v)[kMaxN], double *s_val, int *s_idx) {
+  const int mh = mp.mh, mw = mp.mw, n = mh * mw, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = kBuildThreads / 32;
+  if (tid < n) R[tid / mw][tid % mw] = mp.w[tid];
+  __syncthreads();
+  // argmax of |R| over the mask, ties to the lower index; returns the index
+  auto argmax = [&](double *best) -> int {
+    double val = tid < n ? fabs(R[tid / mw][tid % mw]) : -1.0;
+    int idx = tid < n ? tid : n;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, val, o);
+      const int oi = __shfl_down_sync(0xffffffffu, idx, o);
+      if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+    }
+    if (lane == 0) { s_val[warp] = val; s_idx[warp] = idx; }
+    __syncthreads();
+    double bv = s_val[0];
+    int bi = s_idx[0];
+    for (int w = 1; w < nwarps; ++w)
+      if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bi)) { bv = s_val[w]; bi = s_idx[w]; }
+    __syncthreads();            // s_val / s_idx are reused by the next call
+    *best = bv;
+    return bi;
+  };
+  double wmax;
+  argmax(&wmax);
+  int rank = 0;
+  const int steps = mh < mw ? mh : mw;
+  for (int k = 0; k < steps; ++k) {
+    double best;
+    const int pq = argmax(&best);
+    if (!(best > 1e-13 * wmax)) break;
+    const int p = pq / mw, q = pq % mw;
+    const double piv = R[p][q];
+    if (tid < mh) u[rank][tid] = R[tid][q] / piv;
+    if (tid < mw) v[rank][tid] = R[p][tid];
+    __syncthreads();
+    if (tid < n) R[tid / mw][tid % mw] -= u[rank][tid / mw] * v[rank][tid % mw];
+    __syncthreads();
+    ++rank;
+  }
+  return rank;
+}
 
 // A_t (side 0) or B_t (side 1) of term t = blockIdx.x / 2: the 1-D filter
 // matrix H[i][s] = sum_r f[r] [P(i + r - a) = s], then C H C^T (Eq. 7).
-__global__ void kron_build_kernel(const KronParams kp, const double *__restrict__ C,
-                                  float *__restrict__ A, float *__restrict__ B) {
+__global__ void __launch_bounds__(kBuildThreads)
+kron_build_kernel(const MaskParams mp, const double *__restrict__ C, float *__restrict__ A,
+                  float *__restrict__ B, double *__restrict__ A64, double *__restrict__ B64,
+                  int *__restrict__ rank_out) {
   __shared__ double cs[kMaxN][kMaxN + 1], hs[kMaxN][kMaxN + 1], ts[kMaxN][kMaxN + 1];
-  const int n = kp.n, t = blockIdx.x >> 1, side = blockIdx.x & 1;
+  __shared__ double R[kMaxN][kMaxN], su[kMaxTerms][kMaxN], sv[kMaxTerms][kMaxN];
+  __shared__ double s_val[kBuildThreads / 32];
+  __shared__ int s_idx[kBuildThreads / 32];
+  const int rank = split_mask(mp, R, su, sv, s_val, s_idx);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *rank_out = rank;
+  const int n = mp.n, t = blockIdx.x >> 1, side = blockIdx.x & 1;
+  if (t >= rank) return;
   const int i = threadIdx.x / n, j = threadIdx.x % n;
   const bool live = threadIdx.x < n * n;
-  const double *f = side ? kp.v[t] : kp.u[t];
-  const int len = side ? kp.mw : kp.mh, a = side ? kp.ac : kp.ar;
+  const double *f = side ? sv[t] : su[t];
+  const int len = side ? mp.mw : mp.mh, a = side ? mp.ac : mp.ar;
   if (live) {
     cs[i][j] = C[i * n + j];
     double h = 0.0;                       // entry (i, s = j)
     for (int r = 0; r < len; ++r) {
       int s = i + r - a;
-      if (kp.boundary == DCTF_ZERO) {
+      if (mp.boundary == DCTF_ZERO) {
         if (s < 0 || s >= n) continue;
       } else {
         s = min(max(s, 0), n - 1);
@@ -78,7 +136,82 @@ __global__ void kron_build_kernel(const KronParams kp, const double *__restrict_
   if (live) {                             // C T = C H C^T
     double acc = 0.0;
     for (int p = 0; p < n; ++p) acc += cs[i][p] * ts[p][j];
-    (side ? B : A)[(size_t)t * n * n + i * n + j] = (float)acc;
+    const size_t o = (size_t)t * n * n + i * n + j;
+    (side ? B : A)[o] = (float)acc;
+    (side ? B64 : A64)[o] = acc;
+  }
+}
+
+// n = 16: the FP16 pieces of the factors for the tensor-core form
+// (kron_tc.cu), in the K-major SWIZZLE_128B B-operand layout, and their
+// power-of-two scales.
+//  * Pass 1 operand (16 KB, 128 rows): terms in groups of four; group g uses
+//    the 32-byte K slot g of every 128-byte row, with rows
+//    p * 16 ng + tt * 16 + j for piece p (0 = hi, 1 = lo) of
+//    B_t[j][:] 2^sB, t = 4 g + tt, ng the group's term count.
+//  * Pass 2 operand (16 KB): K block g (4 KB, 32 rows) holds rows p * 16 + i,
+//    elements (tt, k) of piece p of A_t[i][k] 2^sA, t = 4 g + tt.
+//  * sB, sA put the largest factor entry near 2^10, so the lo pieces stay
+//    normal FP16 numbers; sZ makes |Z 2^sZ| <= max |x| for the intermediate
+//    Z_t = X B_t^T (row sums of |B_t| at most 2^-sZ), so the FP16 re-split of
+//    Z cannot overflow where x itself fits FP16.
+//  scale[0] = 2^(sZ - sB) (pass 1 result -> Z 2^sZ), scale[1] = 2^-(sZ + sA).
+__global__ void __launch_bounds__(kBuildThreads)
+kron_pieces_kernel(const double *__restrict__ A64, const double *__restrict__ B64,
+                   const int *__restrict__ rank_in, uint8_t *__restrict__ pieces,
+                   float *__restrict__ scale) {
+  constexpr int n = 16, n2 = 256;
+  __shared__ double red[3][kBuildThreads];
+  const int tid = threadIdx.x, rank = *rank_in;
+  for (int e = tid; e < kKronPieceBytes / 16; e += kBuildThreads)
+    reinterpret_cast<uint4 *>(pieces)[e] = make_uint4(0, 0, 0, 0);
+  double ma = 0.0, mb = 0.0, rs = 0.0;
+  for (int e = tid; e < rank * n2; e += kBuildThreads) {
+    ma = fmax(ma, fabs(A64[e]));
+    mb = fmax(mb, fabs(B64[e]));
+  }
+  for (int e = tid; e < rank * n; e += kBuildThreads) {    // row sums of |B_t|
+    double r = 0.0;
+    for (int l = 0; l < n; ++l) r += fabs(B64[(size_t)e * n + l]);
+    rs = fmax(rs, r);
+  }
+  red[0][tid] = ma; red[1][tid] = mb; red[2][tid] = rs;
+  __syncthreads();
+  for (int w = kBuildThreads / 2; w > 0; w >>= 1) {
+    if (tid < w)
+      for (int k = 0; k < 3; ++k) red[k][tid] = fmax(red[k][tid], red[k][tid + w]);
+    __syncthreads();
+  }
+  ma = red[0][0]; mb = red[1][0]; rs = red[2][0];
+  auto clampi = [](int e) { return e < -40 ? -40 : (e > 40 ? 40 : e); };
+  const int sA = ma > 0.0 ? clampi(10 - (int)ceil(log2(ma))) : 0;
+  const int sB = mb > 0.0 ? clampi(10 - (int)ceil(log2(mb))) : 0;
+  const int sZ = rs > 0.0 ? clampi(-(int)ceil(log2(rs))) : 0;
+  if (tid == 0) {
+    scale[0] = (float)ldexp(1.0, sZ - sB);
+    scale[1] = (float)ldexp(1.0, -(sZ + sA));
+  }
+  __syncthreads();     // the zero fill is complete before the pieces land
+  for (int e = tid; e < rank * n2; e += kBuildThreads) {
+    const int t = e / n2, r = (e / n) % n, c = e % n;      // factor row r, column c
+    const int g = t >> 2, tt = t & 3, ng = min(4, rank - 4 * g);
+    // pass 1: B_t[j = r][l = c]
+    {
+      const double x = ldexp(B64[e], sB);
+      const __half hi = __double2half(x), lo = __double2half(x - (double)__half2float(hi));
+      const int byte = 32 * g + 2 * c;
+      *reinterpret_cast<__half *>(pieces + sw128_offset(tt * 16 + r, byte, 128, 0)) = hi;
+      *reinterpret_cast<__half *>(pieces + sw128_offset(16 * ng + tt * 16 + r, byte, 128, 0)) = lo;
+    }
+    // pass 2: A_t[i = r][k = c]
+    {
+      const double x = ldexp(A64[e], sA);
+      const __half hi = __double2half(x), lo = __double2half(x - (double)__half2float(hi));
+      const int byte = 2 * (tt * 16 + c);
+      uint8_t *p2 = pieces + kKronPieceBytes / 2;
+      *reinterpret_cast<__half *>(p2 + sw128_offset(r, byte, 32, g)) = hi;
+      *reinterpret_cast<__half *>(p2 + sw128_offset(16 + r, byte, 32, g)) = lo;
+    }
   }
 }
 
@@ -90,7 +223,10 @@ template <int N>
 __global__ void __launch_bounds__(kThreads, 2)
 apply_kron_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t nblocks,
                   const float *__restrict__ A, const float *__restrict__ B,
-                  const float *__restrict__ Mdc, int rank) {
+                  const float *__restrict__ Mdc, const int *__restrict__ rank_in, int max_rank) {
+  // the number of terms, from the device build (at most max_rank, which
+  // sized the shared memory)
+  const int rank = min(*rank_in, max_rank);
   constexpr int H = N / 2;                // threads per block
   constexpr int BPC = kThreads / H;       // blocks per pass
   constexpr int LD = N + 4;               // padded row (16-byte aligned, fewer bank conflicts)
@@ -207,7 +343,7 @@ cudaError_t launch_apply(const dctf_operator *op, const float *x, int64_t nblock
                          cudaStream_t s) {
   constexpr int BPC = kThreads / (N / 2), LD = N + 4, UB = N * LD + 4;
   const int smem =
-      (op->krank * N * LD + op->krank * N * N + BPC * UB + N * N) * (int)sizeof(float);
+      (op->krank_bound * N * LD + op->krank_bound * N * N + BPC * UB + N * N) * (int)sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(apply_kron_kernel<N>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -216,60 +352,28 @@ cudaError_t launch_apply(const dctf_operator *op, const float *x, int64_t nblock
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   apply_kron_kernel<N><<<(unsigned)grid, kThreads, smem, s>>>(x, y, nblocks, op->d_kA, op->d_kB,
-                                                             op->d_Mdc, op->krank);
+                                                             op->d_Mdc, op->d_krank,
+                                                             op->krank_bound);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Split the mask into rank-1 terms, w = sum_t u_t v_t^T, by Gaussian
-// elimination with complete pivoting: each step takes the largest remaining
-// entry w[p][q] as pivot, emits u = R[:, q] / R[p][q], v = R[p, :] and
-// subtracts u v^T.  Stops when the remainder is below 1e-13 of the mask's
-// largest entry (the numerical rank).  Returns the number of terms.
-int kron_split_mask(const MaskParams &mp, double (*u)[kMaxN], double (*v)[kMaxN]) {
-  const int mh = mp.mh, mw = mp.mw;
-  double R[kMaxN][kMaxN];
-  double wmax = 0.0;
-  for (int r = 0; r < mh; ++r)
-    for (int c = 0; c < mw; ++c) {
-      R[r][c] = mp.w[r * mw + c];
-      wmax = fmax(wmax, fabs(R[r][c]));
-    }
-  int rank = 0;
-  const int steps = mh < mw ? mh : mw;
-  for (int k = 0; k < steps; ++k) {
-    int p = 0, q = 0;
-    double best = -1.0;
-    for (int r = 0; r < mh; ++r)
-      for (int c = 0; c < mw; ++c)
-        if (fabs(R[r][c]) > best) { best = fabs(R[r][c]); p = r; q = c; }
-    if (!(best > 1e-13 * wmax)) break;
-    const double piv = R[p][q];
-    for (int r = 0; r < mh; ++r) u[rank][r] = R[r][q] / piv;
-    for (int c = 0; c < mw; ++c) v[rank][c] = R[p][c];
-    for (int r = 0; r < mh; ++r)
-      for (int c = 0; c < mw; ++c) R[r][c] -= u[rank][r] * v[rank][c];
-    ++rank;
-  }
-  return rank;
-}
-
 cudaError_t launch_kron_build(dctf_operator *op, const MaskParams &mp, cudaStream_t s) {
-  KronParams kp;
-  memset(&kp, 0, sizeof kp);
-  kp.rank = kron_split_mask(mp, kp.u, kp.v);
-  kp.mh = mp.mh; kp.mw = mp.mw; kp.ar = mp.ar; kp.ac = mp.ac;
-  kp.n = mp.n; kp.boundary = mp.boundary;
-  op->krank = kp.rank;
-  if (kp.rank == 0) return cudaSuccess;   // zero mask: nothing to apply, output zeros
-  kron_build_kernel<<<2 * kp.rank, kMaxN2, 0, s>>>(kp, op->d_C64, op->d_kA, op->d_kB);
-  return cudaGetLastError();
+  op->krank_bound = mp.mh < mp.mw ? mp.mh : mp.mw;
+  kron_build_kernel<<<2 * op->krank_bound, kBuildThreads, 0, s>>>(
+      mp, op->d_C64, op->d_kA, op->d_kB, op->d_kA64, op->d_kB64, op->d_krank);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && op->d_kpieces != nullptr) {
+    kron_pieces_kernel<<<1, kBuildThreads, 0, s>>>(op->d_kA64, op->d_kB64, op->d_krank,
+                                                   op->d_kpieces, op->d_kscale);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 cudaError_t launch_apply_kron(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
                               cudaStream_t s) {
-  if (op->krank == 0) return cudaMemsetAsync(y, 0, (size_t)nblocks * op->n2 * sizeof(float), s);
   switch (op->n) {
     case 4: return launch_apply<4>(op, x, nblocks, y, s);
     case 8: return launch_apply<8>(op, x, nblocks, y, s);

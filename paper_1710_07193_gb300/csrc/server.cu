@@ -434,15 +434,23 @@ void worker_loop(dctf_server *s) {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop && s->pending.empty() && !any_busy) break;
       if (free_slot) {
+        // A batch holds its arena bytes until all of it has retired, so one
+        // batch may take at most a quarter of the budget (a request larger
+        // than that goes alone): several batches are then in flight, and one
+        // batch's copies back overlap the next one's copies in and kernel.
+        const size_t cap_bytes = s->cfg.hbm_budget_bytes / 4;
         int planes = 0;
+        size_t batch_bytes = 0;
         while (!s->pending.empty() && (int)batch.size() < s->cfg.max_batch_requests) {
           Req *r = s->pending.front();
           if (planes + r->nplanes > free_slot->cap) break;
+          if (!batch.empty() && r->bytes > 0 && batch_bytes + r->bytes > cap_bytes) break;
           if (r->bytes > 0 && !s->arena.alloc(r->bytes, &r->off)) {   // wait for memory
             if (!r->waited) { r->waited = true; ++s->budget_waits; }
             break;
           }
           s->hbm_peak = std::max(s->hbm_peak, s->arena.used());
+          batch_bytes += r->bytes;
           s->pending.pop_front();
           planes += r->nplanes;
           batch.push_back(r);

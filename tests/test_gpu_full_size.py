@@ -120,12 +120,12 @@ def large_full():
 
 
 @pytest.mark.parametrize("prec", ["F16X3", "BF16X6", "TF32X3", "FP32_SIMT", "BF16X3", "TF32X1",
-                                  "KRON_FP32"])
+                                  "KRON_FP32", "KRON_F16X3"])
 def test_large_16x16_full_workload(dctf, large_full, prec):
     job, p_sp, x, m = large_full
     nb = x.shape[0]
     assert nb == 262144
-    op = dctf.build_operator(job.mask, job.anchor, 16, job.boundary, kron=(prec == "KRON_FP32"))
+    op = dctf.build_operator(job.mask, job.anchor, 16, job.boundary, kron=prec.startswith("KRON"))
     op.set_precision(getattr(dctf, prec))
     xd = torch.from_numpy(x).cuda()
     yd = torch.full_like(xd, float("nan"))

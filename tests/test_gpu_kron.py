@@ -121,3 +121,99 @@ def test_kron_convolution(dctf):
     for b in range(7):
         assert np.abs(p[b] - nd.convolve(blocks[b], w, mode="nearest")).max() < 2e-3
     op.release()
+
+
+# ------------------------------------------- the sandwich products on tensor cores
+TC_CASES = [   # mask, anchor, boundary, expected rank (terms: 1-4 groups of four)
+    ("gauss7", (3, 3), 0, 1),
+    ("gauss9", (4, 4), 1, 1),
+    ("laplacian", (1, 1), 1, 2),
+    ("magic", (1, 1), 1, 3),
+    ("rand5", (1, 3), 0, 5),
+    ("large", (4, 4), 1, 9),
+    ("rand16", (7, 2), 1, 16),
+]
+
+
+def tc_mask(name):
+    g = np.random.default_rng(64)
+    if name == "gauss9":
+        return datagen.gaussian_mask(9, 2.5)
+    if name == "rand5":
+        return g.uniform(-1, 1, (5, 5))
+    if name == "rand16":
+        w = g.uniform(-1, 1, (16, 16))
+        return w / w.sum()
+    return mask_of(name)
+
+
+@pytest.fixture(scope="module")
+def tc_source():
+    img = datagen.synthetic_image(512, 768, datagen.rng(98, 200, 0))
+    blocks = oracle.image_to_blocks(img, 16)
+    return blocks, oracle.dct2_blocks(blocks).astype(np.float32)
+
+
+@pytest.mark.parametrize("case", range(len(TC_CASES)))
+def test_kron_tc_matches_oracle(dctf, tc_source, case):
+    """DCTF_KRON_F16X3: Z_t = X B_t^T and Y = sum_t A_t Z_t as F16X3
+    tensor-core products, held to the same bars as every exact arithmetic."""
+    name, a, bnd, rank = TC_CASES[case]
+    w = tc_mask(name)
+    blocks, x = tc_source
+    op = dctf.build_operator(w, a, 16, bnd, kron=True)
+    assert op.kron_rank() == rank == len(oracle.mask_rank_terms(w))
+    op.set_precision(dctf.KRON_F16X3)
+    y = run(dctf, op, x)
+    assert op.status() == 0
+    y_ref = oracle.apply_M(oracle.build_M(w, a, 16, bnd), x.astype(np.float64))
+    assert np.abs(y - y_ref).max() <= COEF_TOL * max(1.0, abs(w.sum()))
+    # the same operator in its Kronecker form, applied by the oracle
+    y_kron = oracle.apply_kron(oracle.kron_factors(w, a, 16, bnd), x, 16)
+    assert np.abs(y - y_kron).max() <= COEF_TOL * max(1.0, abs(w.sum()))
+    st = oracle.uint8_compare(oracle.spatial_filter_blocks(blocks, w, a, bnd),
+                              oracle.to_uint8(oracle.idct2_blocks(y, 16)), BAND)
+    assert st["mismatch"] == 0, st
+    op.release()
+
+
+@pytest.mark.parametrize("nb", [1, 7, 8, 9, 1000, 40001])
+def test_kron_tc_ragged_and_in_place(dctf, nb):
+    """Units of 8 blocks: counts that leave a partial unit and CTAs without
+    work; in place gives the same bits."""
+    img = datagen.synthetic_image(3200, 3200, datagen.rng(98, 101, 0))
+    x = oracle.dct2_blocks(oracle.image_to_blocks(img, 16))[:nb].astype(np.float32)
+    w, a = datagen.large_mask(), (4, 4)
+    op = dctf.build_operator(w, a, 16, dctf.REPLICATE, kron=True)
+    op.set_precision(dctf.KRON_F16X3)
+    y = run(dctf, op, x)
+    y_ref = oracle.apply_M(oracle.build_M(w, a, 16, oracle.REPLICATE), x.astype(np.float64))
+    assert np.abs(y - y_ref).max() <= COEF_TOL
+    assert np.array_equal(run(dctf, op, x, inplace=True), y)
+    assert op.status() == 0
+    op.release()
+
+
+def test_kron_tc_rebuild_zero_mask_and_support(dctf, tc_source):
+    """The number of terms is read on the device at each launch: a rebuild
+    that changes it needs nothing from the host; a zero mask (no terms)
+    filters to zero; the variant exists for 16 x 16 blocks only."""
+    _, x = tc_source
+    op = dctf.build_operator(datagen.gaussian_mask(9, 2.5), (4, 4), 16, dctf.ZERO, kron=True)
+    op.set_precision(dctf.KRON_F16X3)
+    for w, a, bnd in ((datagen.magic_square_3(), (1, 1), 1), (tc_mask("rand5"), (2, 2), 0),
+                      (datagen.gaussian_mask(3, 1.0), (1, 1), 1)):
+        op.rebuild(w, a, bnd)
+        y = run(dctf, op, x)
+        y_ref = oracle.apply_M(oracle.build_M(w, a, 16, bnd), x.astype(np.float64))
+        assert np.abs(y - y_ref).max() <= COEF_TOL * max(1.0, abs(w.sum()))
+    op.rebuild(np.zeros((5, 5)), (2, 2), dctf.ZERO)
+    assert op.kron_rank() == 0
+    assert not run(dctf, op, x).any()
+    assert op.status() == 0
+    op.release()
+    op8 = dctf.build_operator(datagen.gaussian_mask(3, 1.0), (1, 1), 8, dctf.ZERO, kron=True)
+    with pytest.raises(dctf.DctfError) as e:
+        op8.set_precision(dctf.KRON_F16X3)
+    assert e.value.status == 6
+    op8.release()

@@ -236,13 +236,14 @@ def test_admission_waits_for_budget(dctf):
     budget = 1 << 20
     srv = dctf.Server(hbm_budget_bytes=budget, max_inflight=4, max_batch_requests=4,
                       staged_only=True)
-    g = np.random.default_rng(21)
     w, a, bnd = datagen.serving_mask(3)
     m = oracle.build_M(w, a, 8, bnd)
-    q, qo = datagen.quant_table(2).ravel(), datagen.quant_table(1).ravel()
+    qo = datagen.quant_table(1).ravel()
     reqs = []
     for k in range(5):
-        x = g.integers(-400, 400, (3072, 64)).astype(np.int16)     # 384 KiB a plane
+        # a 384 x 512 image's quantised coefficients: 3072 blocks, 384 KiB
+        img = datagen.synthetic_image(384, 512, datagen.rng(97, k, 0))
+        x, q = quantised(img, 2)
         xin = torch.from_numpy(x).pin_memory()                      # page-locked, yet staged
         xout = torch.zeros_like(xin).pin_memory()
         reqs.append((x, xin, xout))
