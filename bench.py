@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--serving-requests", type=int, default=10000)
     p.add_argument("--no-workloads", action="store_true",
                    help="skip the small / grouped / 16x16 workloads")
+    p.add_argument("--serving-only", action="store_true",
+                   help="run only the serving phase (rank 0) and print its JSON; not a bench "
+                        "line")
     p.add_argument("--workloads-only", action="store_true",
                    help="run only the small / grouped / 16x16 workloads (rank 0) and print "
                         "their JSON; not a bench line (for profiling them)")
@@ -596,6 +599,11 @@ def run_dctf(args):
     if args.workloads_only:
         if rank == 0:
             print(json.dumps({"workloads": run_workloads(lib, torch, 40)}), flush=True)
+        return
+    if args.serving_only:
+        if rank == 0:
+            print(json.dumps({"serving": run_serving(lib, torch, args.serving_requests)}),
+                  flush=True)
         return
 
     job = datagen.headline_job(args.size, args.size)
