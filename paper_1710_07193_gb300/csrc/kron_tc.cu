@@ -24,9 +24,14 @@
 //  pass 2  Y = sum_t A_t Z_t: rows (block b, column j), K = (term, k),
 //          N = (piece, i); B = the hi and lo pieces of A_t 2^sA stacked along
 //          N, so per term
-//            D2 = Z_hi [A_hi | A_lo]^T   (N = 32)
-//            D2[:, A_hi part] += Z_lo A_hi^T   (N = 16).
-//  epilogue  y[b][i][j] = (D2[i] + D2[16 + i]) 2^-(sZ + sA) + M[(i,j), 0] x0,
+//            D2[:, 0:32] (+)= Z_hi [A_hi | A_lo]^T   (N = 32)
+//            D2[:, 32:48] (+)= Z_lo A_hi^T           (N = 16).
+//          The main product Z_hi A_hi has its 16 columns to itself: tensor-
+//          core FP32 accumulation truncates, and keeping the corrections in
+//          their own columns halves the chain of truncating adds that reach
+//          the largest sums (a full-rank 16x16 mask: 16 instead of 32).
+//  epilogue  y[b][i][j] = (D2[i] + (D2[16 + i] + D2[32 + i])) 2^-(sZ + sA)
+//          + M[(i,j), 0] x0,
 //          the DC term kept out of the products and applied in FP32 as in
 //          the dense kernels; staged per block and written with 1 KB bulk
 //          copies.
@@ -57,9 +62,9 @@ constexpr int kUnitBytes = kUnit * kN2 * 4;   // 8 KB: one TMA box of 32 floats 
 constexpr int kStages = 12;
 constexpr int kMaxTerms = 16;
 constexpr int kDcRing = 8;
-// TMEM columns (512 allocated): every buffer aligned to 32 columns
-constexpr uint32_t kColA1 = 0;      // 2 x 32 (16 used): x hi (8) | x lo (8)
-constexpr uint32_t kColD2 = 64;     // 2 x 32: pass-2 accumulators
+// TMEM columns (512 allocated), every buffer aligned to 16 columns
+constexpr uint32_t kColA1 = 0;      // 2 x 16: x hi (8) | x lo (8)
+constexpr uint32_t kColD2 = 32;     // 2 x 48: main | Z_hi A_lo | Z_lo A_hi
 constexpr uint32_t kColD1 = 128;    // 2 x 128: pass-1 accumulators
 constexpr uint32_t kColA2 = 384;    // 2 x 64: Z hi (32) | Z lo (32), four terms
 constexpr uint32_t kTmemCols = 512;
@@ -192,7 +197,7 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
         if (!wait_bounded(&d1_empty[db], ((st >> 1) & 1) ^ 1, s_abort, err, kRoleMma | (st << 8)))
           goto mma_done;
         tc_fence_after();
-        const uint32_t t_a1 = tmem + kColA1 + ab * 32, t_d1 = tmem + kColD1 + db * 128;
+        const uint32_t t_a1 = tmem + kColA1 + ab * 16, t_d1 = tmem + kColD1 + db * 128;
         const uint64_t b1 = desc_sw128(smem_u32(s_b1)) + 2 * g;     // K slot g
         mma_f16_ts(t_d1, t_a1, b1, idesc_f16(128, 32 * ng, false), 0u);
         mma_f16_ts(t_d1, t_a1 + 8, b1, idesc_f16(128, 16 * ng, false), 1u);
@@ -201,8 +206,8 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
         if (g == NG - 1) tc_commit(&a1_empty[ab]);
       }
       if (st >= 1) {
-        // pass 2 of step st - 1: per term, D2 = Z_hi [A_hi | A_lo]^T,
-        // then += Z_lo A_hi^T
+        // pass 2 of step st - 1: per term, D2[0:32] = Z_hi [A_hi | A_lo]^T,
+        // D2[32:48] = Z_lo A_hi^T
         const int sp = st - 1, k = sp / NG, g = sp % NG, ng = min(4, rank - 4 * g);
         const int a2b = sp & 1, d2b = k & 1;
         if (!wait_bounded(&a2_full[a2b], (sp >> 1) & 1, s_abort, err, kRoleMma | (sp << 8)))
@@ -211,12 +216,12 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
             !wait_bounded(&d2_empty[d2b], ((k >> 1) & 1) ^ 1, s_abort, err, kRoleMma | (sp << 8)))
           goto mma_done;
         tc_fence_after();
-        const uint32_t t_a2 = tmem + kColA2 + a2b * 64, t_d2 = tmem + kColD2 + d2b * 32;
+        const uint32_t t_a2 = tmem + kColA2 + a2b * 64, t_d2 = tmem + kColD2 + d2b * 48;
         const uint64_t b2 = desc_sw128(smem_u32(s_b2 + g * 4096));   // K block g
         for (int tt = 0; tt < ng; ++tt) {
-          mma_f16_ts(t_d2, t_a2 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 32, false),
-                     (g > 0 || tt > 0) ? 1u : 0u);
-          mma_f16_ts(t_d2, t_a2 + 32 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 16, false), 1u);
+          const uint32_t acc = (g > 0 || tt > 0) ? 1u : 0u;
+          mma_f16_ts(t_d2, t_a2 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 32, false), acc);
+          mma_f16_ts(t_d2 + 32, t_a2 + 32 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 16, false), acc);
         }
         tc_commit(&a2_empty[a2b]);
         last_bar = &a2_empty[a2b]; last_ph = (sp >> 1) & 1;
@@ -261,7 +266,7 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
       tc_fence_after();
       uint32_t hi[8], lo[8];
       split16(v, hi, lo);
-      const uint32_t t_a1 = tmem + lane_base + kColA1 + (k & 1) * 32;
+      const uint32_t t_a1 = tmem + lane_base + kColA1 + (k & 1) * 16;
       tmem_st8(t_a1, hi);
       tmem_st8(t_a1 + 8, lo);
       tmem_st_wait();
@@ -328,13 +333,15 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
         if (!warp_wait_bounded(&d2_full[k & 1], (k >> 1) & 1, s_abort, err, kRoleEpi | (k << 8)))
           break;
         tc_fence_after();
-        uint32_t d[32];
-        tmem_ld32(tmem + lane_base + kColD2 + (k & 1) * 32, d);
+        uint32_t dm[16], c1[16], c2[16];
+        const uint32_t t_d2 = tmem + lane_base + kColD2 + (k & 1) * 48;
+        tmem_ld16x3(t_d2, t_d2 + 16, t_d2 + 32, dm, c1, c2);
         tc_fence_before();
         mbar_arrive(&d2_empty[k & 1]);
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          acc[i] = (__uint_as_float(d[i]) + __uint_as_float(d[16 + i])) * oscale;
+          acc[i] = (__uint_as_float(dm[i]) + (__uint_as_float(c1[i]) + __uint_as_float(c2[i]))) *
+                   oscale;
       } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) acc[i] = 0.f;

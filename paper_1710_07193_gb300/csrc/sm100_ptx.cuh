@@ -365,6 +365,23 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, uint32_t (
       : "memory");
 }
 
+// Three 16-column loads of this lane's row, one wait for all.
+__device__ __forceinline__ void tmem_ld16x3(uint32_t ta, uint32_t tb, uint32_t tc,
+                                            uint32_t (&a)[16], uint32_t (&b)[16],
+                                            uint32_t (&c)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%48];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%49];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%50];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : DCTF_W16(a, 0), DCTF_W16(b, 0), DCTF_W16(c, 0)
+      : "r"(ta), "r"(tb), "r"(tc)
+      : "memory");
+}
+
 // Untiled bulk copy shared -> global in the thread's bulk group (both
 // addresses 16-byte aligned, size a multiple of 16).
 __device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
