@@ -9,18 +9,19 @@
 // blocks (128 MMA rows):
 //
 //  pass 1  Z_t = X B_t^T for every term: rows (block b, row k of X), K = the
-//          16 columns of X, N = (piece, term, j).  The B operand stacks the
-//          hi and lo pieces of B_t 2^sB along N, so
-//            D1 = x_hi [B_hi | B_lo]^T   (N = 32 ng)
-//            D1[:, B_hi part] += x_lo B_hi^T   (N = 16 ng)
-//          gives x_hi B_hi + x_hi B_lo + x_lo B_hi in two MMAs per group of
-//          up to four terms.
+//          16 columns of X, N = (term, j).  The B operand holds the hi pieces
+//          of B_t 2^sB, then the lo pieces, so
+//            D1 = x_hi B_lo^T + x_lo B_hi^T + x_hi B_hi^T
+//          (corrections first, while the sum is small) is three MMAs of
+//          N = 16 ng per group of up to four terms.
 //  transpose  pass 2 contracts over k, which pass 1 leaves in TMEM lanes.
 //          A transposer thread (lane (b, k)) reads its row of Z_t, puts it
 //          through a padded 16 x 20 shared-memory tile of its block, reads
 //          back column j = its row index (now lane (b, j)), re-splits it
 //          into FP16 hi/lo (Z 2^sZ, scaled so it cannot overflow FP16) and
-//          stores it to its own TMEM lane as pass 2's A operand.
+//          stores it to its own TMEM lane as pass 2's A operand.  Two warp
+//          sets take alternate steps, so one set's latency hides under the
+//          other's work.
 //  pass 2  Y = sum_t A_t Z_t: rows (block b, column j), K = (term, k),
 //          N = (piece, i); B = the hi and lo pieces of A_t 2^sA stacked along
 //          N, so per term
@@ -36,16 +37,19 @@
 //          the dense kernels; staged per block and written with 1 KB bulk
 //          copies.
 //
-// So a unit costs 2 + 2 r MMAs whatever their width, against the dense
-// kernel's 3 x 256 x 256 MAC per block, and the data movement stays the
-// dense kernel's 2 KB a block.  The factors' pieces and scales come from the
-// FP64 device build (kron.cu); the number of terms is read on the device.
+// So a unit costs 3 + 2 r MMAs (r <= 4; 3 more per further group of four
+// terms), against the dense kernel's 3 x 256 x 256 MAC per block, and the
+// data movement stays the dense kernel's 2 KB a block.  The factors' pieces
+// and scales come from the FP64 device build (kron.cu); the number of terms
+// is read on the device.
 //
-// Roles (512 threads): warp 0 TMA producer (one 8 KB box per unit), warp 1
-// MMA issuer (pass 1 of step s, then pass 2 of step s - 1, so the transposer
-// works under the next pass 1), warp 2 TMEM allocator, warps 4-7 converter
-// (thread = row (b, k): DC out, FP16 split, A1 to TMEM), warps 8-11
-// transposer, warps 12-15 epilogue.  Every wait is bounded (sm100_ptx.cuh).
+// Roles (640 threads): warp 0 TMA producer (one 8 KB box per unit), warp 1
+// MMA issuer, warp 2 TMEM allocator, warps 4-7 converter (thread = row
+// (b, k): DC out, FP16 split, A1 to TMEM), warps 8-11 and 16-19 transposer
+// (even and odd steps), warps 12-15 epilogue.  The MMA issuer polls both
+// passes' queues and issues whichever is ready, so pass 1 runs ahead of the
+// transposers instead of waiting behind them.  Every wait is bounded
+// (sm100_ptx.cuh).
 #include "sm100_ptx.cuh"
 
 #include <mutex>
@@ -56,17 +60,18 @@ namespace {
 using namespace ptx;
 
 constexpr int kN2 = 256;
-constexpr int kThreads = 512;
+constexpr int kThreads = 640;
 constexpr int kUnit = 8;                      // blocks per unit: 128 MMA rows
 constexpr int kUnitBytes = kUnit * kN2 * 4;   // 8 KB: one TMA box of 32 floats x 64 lines
 constexpr int kStages = 12;
 constexpr int kMaxTerms = 16;
 constexpr int kDcRing = 8;
 // TMEM columns (512 allocated), every buffer aligned to 16 columns
-constexpr uint32_t kColA1 = 0;      // 2 x 16: x hi (8) | x lo (8)
-constexpr uint32_t kColD2 = 32;     // 2 x 48: main | Z_hi A_lo | Z_lo A_hi
-constexpr uint32_t kColD1 = 128;    // 2 x 128: pass-1 accumulators
-constexpr uint32_t kColA2 = 384;    // 2 x 64: Z hi (32) | Z lo (32), four terms
+constexpr int kA1Bufs = 4;
+constexpr uint32_t kColA1 = 0;      // 4 x 16: x hi (8) | x lo (8)
+constexpr uint32_t kColD2 = 64;     // 2 x 48: main | Z_hi A_lo | Z_lo A_hi
+constexpr uint32_t kColD1 = 160;    // 2 x 64: pass-1 accumulators (16 per term)
+constexpr uint32_t kColA2 = 288;    // 2 x 64: Z hi (32) | Z lo (32), four terms
 constexpr uint32_t kTmemCols = 512;
 // shared memory
 constexpr int kTRow = 20;                     // transposer tile row (floats)
@@ -76,11 +81,11 @@ constexpr int kOffIn = 0;
 constexpr int kOffB1 = kOffIn + kStages * kUnitBytes;     // 16 KB pass-1 pieces
 constexpr int kOffB2 = kOffB1 + kKronPieceBytes / 2;      // 16 KB pass-2 pieces
 constexpr int kOffT = kOffB2 + kKronPieceBytes / 2;
-constexpr int kOffOut = kOffT + 4 * 2 * kTBlk * 4;
+constexpr int kOffOut = kOffT + 2 * 4 * 2 * kTBlk * 4;   // two transposer sets
 constexpr int kOffMdc = kOffOut + 4 * 2 * 2 * kOutBlk * 4;
 constexpr int kOffDc = kOffMdc + kN2 * 4;
 constexpr int kOffBar = kOffDc + kDcRing * kUnit * 4;
-constexpr int kNumBars = 2 * kStages + 8 * 2 + 2 * kDcRing;
+constexpr int kNumBars = 2 * kStages + 2 * kA1Bufs + 6 * 2 + 2 * kDcRing;
 constexpr int kOffMisc = kOffBar + kNumBars * 8;
 constexpr int kSmem = kOffMisc + 16 + 1024;
 static_assert(kSmem <= 232448, "shared memory");
@@ -121,9 +126,9 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + kOffBar);
   uint64_t *full_in = bars;                   // [kStages] TMA -> converter
   uint64_t *empty_in = full_in + kStages;     // [kStages] converter -> TMA
-  uint64_t *a1_full = empty_in + kStages;     // [2] converter -> MMA
-  uint64_t *a1_empty = a1_full + 2;           // [2] MMA (pass 1 done) -> converter
-  uint64_t *d1_full = a1_empty + 2;           // [2] MMA -> transposer
+  uint64_t *a1_full = empty_in + kStages;     // [kA1Bufs] converter -> MMA
+  uint64_t *a1_empty = a1_full + kA1Bufs;     // [kA1Bufs] MMA (pass 1 done) -> converter
+  uint64_t *d1_full = a1_empty + kA1Bufs;     // [2] MMA -> transposer
   uint64_t *d1_empty = d1_full + 2;           // [2] transposer -> MMA
   uint64_t *a2_full = d1_empty + 2;           // [2] transposer -> MMA
   uint64_t *a2_empty = a2_full + 2;           // [2] MMA (pass 2 done) -> transposer
@@ -145,8 +150,8 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(&full_in[s], 1); mbar_init(&empty_in[s], 128); }
+    for (int b = 0; b < kA1Bufs; ++b) { mbar_init(&a1_full[b], 128); mbar_init(&a1_empty[b], 1); }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&a1_full[b], 128); mbar_init(&a1_empty[b], 1);
       mbar_init(&d1_full[b], 1);   mbar_init(&d1_empty[b], 128);
       mbar_init(&a2_full[b], 128); mbar_init(&a2_empty[b], 1);
       mbar_init(&d2_full[b], 1);   mbar_init(&d2_empty[b], 128);
@@ -184,51 +189,69 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
       wait_drain(&full_in[k % kStages], (k / kStages) & 1, err, kRoleDrain);
   } else if (warp == 1 && lane == 0 && terms) {
     // ---------------------------------------------------------- MMA issuer
+    // Two queues: pass 1 of step n1 (needs the unit's A1 and a free D1
+    // buffer) and pass 2 of step n2 < n1 (needs the step's A2 from a
+    // transposer and, at a unit's first group, a free D2).  Each round
+    // issues whatever is ready; a round without progress polls again, and
+    // after kWaitLimitNs without progress the launch gives up.
     uint64_t *last_bar = nullptr;
     uint32_t last_ph = 0;
-    for (int st = 0; st <= nsteps; ++st) {
-      if (st < nsteps) {
-        // pass 1 of step st: D1 = x_hi [B_hi | B_lo]^T, then += x_lo B_hi^T
-        const int k = st / NG, g = st % NG, ng = min(4, rank - 4 * g);
-        const int ab = k & 1, db = st & 1;
-        if (g == 0 &&
-            !wait_bounded(&a1_full[ab], (k >> 1) & 1, s_abort, err, kRoleMma | (st << 8)))
-          goto mma_done;
-        if (!wait_bounded(&d1_empty[db], ((st >> 1) & 1) ^ 1, s_abort, err, kRoleMma | (st << 8)))
-          goto mma_done;
-        tc_fence_after();
-        const uint32_t t_a1 = tmem + kColA1 + ab * 16, t_d1 = tmem + kColD1 + db * 128;
-        const uint64_t b1 = desc_sw128(smem_u32(s_b1)) + 2 * g;     // K slot g
-        mma_f16_ts(t_d1, t_a1, b1, idesc_f16(128, 32 * ng, false), 0u);
-        mma_f16_ts(t_d1, t_a1 + 8, b1, idesc_f16(128, 16 * ng, false), 1u);
-        tc_commit(&d1_full[db]);
-        last_bar = &d1_full[db]; last_ph = (st >> 1) & 1;
-        if (g == NG - 1) tc_commit(&a1_empty[ab]);
-      }
-      if (st >= 1) {
-        // pass 2 of step st - 1: per term, D2[0:32] = Z_hi [A_hi | A_lo]^T,
-        // D2[32:48] = Z_lo A_hi^T
-        const int sp = st - 1, k = sp / NG, g = sp % NG, ng = min(4, rank - 4 * g);
-        const int a2b = sp & 1, d2b = k & 1;
-        if (!wait_bounded(&a2_full[a2b], (sp >> 1) & 1, s_abort, err, kRoleMma | (sp << 8)))
-          goto mma_done;
-        if (g == 0 &&
-            !wait_bounded(&d2_empty[d2b], ((k >> 1) & 1) ^ 1, s_abort, err, kRoleMma | (sp << 8)))
-          goto mma_done;
-        tc_fence_after();
-        const uint32_t t_a2 = tmem + kColA2 + a2b * 64, t_d2 = tmem + kColD2 + d2b * 48;
-        const uint64_t b2 = desc_sw128(smem_u32(s_b2 + g * 4096));   // K block g
-        for (int tt = 0; tt < ng; ++tt) {
-          const uint32_t acc = (g > 0 || tt > 0) ? 1u : 0u;
-          mma_f16_ts(t_d2, t_a2 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 32, false), acc);
-          mma_f16_ts(t_d2 + 32, t_a2 + 32 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 16, false), acc);
+    int n1 = 0, n2 = 0;
+    uint64_t t_progress = globaltimer();
+    while (n2 < nsteps) {
+      bool progressed = false;
+      if (n1 < nsteps) {
+        const int k = n1 / NG, g = n1 % NG, ng = min(4, rank - 4 * g);
+        const int ab = k % kA1Bufs, db = n1 & 1;
+        if ((g != 0 || mbar_test_wait(&a1_full[ab], (k / kA1Bufs) & 1)) &&
+            mbar_test_wait(&d1_empty[db], ((n1 >> 1) & 1) ^ 1)) {
+          tc_fence_after();
+          const uint32_t t_a1 = tmem + kColA1 + ab * 16, t_d1 = tmem + kColD1 + db * 64;
+          const uint32_t idesc = idesc_f16(128, 16 * ng, false);
+          const uint64_t b_hi = desc_sw128(smem_u32(s_b1)) + 2 * g;              // K slot g
+          const uint64_t b_lo = desc_sw128(smem_u32(s_b1 + 16 * ng * 128)) + 2 * g;
+          mma_f16_ts(t_d1, t_a1, b_lo, idesc, 0u);          // x_hi B_lo
+          mma_f16_ts(t_d1, t_a1 + 8, b_hi, idesc, 1u);      // x_lo B_hi
+          mma_f16_ts(t_d1, t_a1, b_hi, idesc, 1u);          // x_hi B_hi
+          tc_commit(&d1_full[db]);
+          last_bar = &d1_full[db]; last_ph = (n1 >> 1) & 1;
+          if (g == NG - 1) tc_commit(&a1_empty[ab]);
+          ++n1;
+          progressed = true;
         }
-        tc_commit(&a2_empty[a2b]);
-        last_bar = &a2_empty[a2b]; last_ph = (sp >> 1) & 1;
-        if (g == NG - 1) tc_commit(&d2_full[d2b]);
+      }
+      if (n2 < n1) {
+        const int k = n2 / NG, g = n2 % NG, ng = min(4, rank - 4 * g);
+        const int a2b = n2 & 1, d2b = k & 1;
+        if (mbar_test_wait(&a2_full[a2b], (n2 >> 1) & 1) &&
+            (g != 0 || mbar_test_wait(&d2_empty[d2b], ((k >> 1) & 1) ^ 1))) {
+          tc_fence_after();
+          const uint32_t t_a2 = tmem + kColA2 + a2b * 64, t_d2 = tmem + kColD2 + d2b * 48;
+          const uint64_t b2 = desc_sw128(smem_u32(s_b2 + g * 4096));   // K block g
+          for (int tt = 0; tt < ng; ++tt) {
+            const uint32_t acc = (g > 0 || tt > 0) ? 1u : 0u;
+            mma_f16_ts(t_d2, t_a2 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 32, false), acc);
+            mma_f16_ts(t_d2 + 32, t_a2 + 32 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 16, false),
+                       acc);
+          }
+          tc_commit(&a2_empty[a2b]);
+          last_bar = &a2_empty[a2b]; last_ph = (n2 >> 1) & 1;
+          if (g == NG - 1) tc_commit(&d2_full[d2b]);
+          ++n2;
+          progressed = true;
+        }
+      }
+      if (progressed) {
+        t_progress = globaltimer();
+      } else {
+        if (*s_abort) break;
+        if (globaltimer() - t_progress > kWaitLimitNs) {
+          atomicCAS(err, 0u, kRoleMma | (n2 << 8));
+          *s_abort = 1;
+          break;
+        }
       }
     }
-  mma_done:
     // every MMA issued so far has completed once the last commit arrived
     if (last_bar != nullptr) wait_drain(last_bar, last_ph, err, kRoleDrain);
   } else if (warp >= 4 && warp < 8) {
@@ -260,38 +283,40 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
       if (r == 0) s_dc[slot * kUnit + lb] = x0;
       mbar_arrive(&dc_full[slot]);
       if (!terms) continue;
-      if (!warp_wait_bounded(&a1_empty[k & 1], ((k >> 1) & 1) ^ 1, s_abort, err,
+      if (!warp_wait_bounded(&a1_empty[k % kA1Bufs], ((k / kA1Bufs) & 1) ^ 1, s_abort, err,
                              kRoleConv | (k << 8)))
         break;
       tc_fence_after();
       uint32_t hi[8], lo[8];
       split16(v, hi, lo);
-      const uint32_t t_a1 = tmem + lane_base + kColA1 + (k & 1) * 16;
+      const uint32_t t_a1 = tmem + lane_base + kColA1 + (k % kA1Bufs) * 16;
       tmem_st8(t_a1, hi);
       tmem_st8(t_a1 + 8, lo);
       tmem_st_wait();
       tc_fence_before();
-      mbar_arrive(&a1_full[k & 1]);
+      mbar_arrive(&a1_full[k % kA1Bufs]);
     }
-  } else if (warp >= 8 && warp < 12 && terms) {
+  } else if (((warp >= 8 && warp < 12) || warp >= 16) && terms) {
     // ---------------------------------------------------------- transposer
-    const int q = warp & 3, lb = lane >> 4, r = lane & 15;
+    // warps 8-11 take the even steps (D1 and A2 buffers 0), warps 16-19
+    // the odd ones (buffers 1)
+    const int q = warp & 3, lb = lane >> 4, r = lane & 15, db = warp >= 16 ? 1 : 0;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const float zscale = __ldg(kscale);
-    float *tile = s_t + (q * 2 + lb) * kTBlk;
-    for (int st = 0; st < nsteps; ++st) {
-      const int g = st % NG, ng = min(4, rank - 4 * g), db = st & 1;
+    float *tile = s_t + ((db * 4 + q) * 2 + lb) * kTBlk;
+    const uint32_t t_d1 = tmem + lane_base + kColD1 + db * 64;
+    const uint32_t t_a2 = tmem + lane_base + kColA2 + db * 64;
+    for (int st = db; st < nsteps; st += 2) {
+      const int g = st % NG, ng = min(4, rank - 4 * g);
       if (!warp_wait_bounded(&d1_full[db], (st >> 1) & 1, s_abort, err, kRoleTrans | (st << 8)))
         break;
       tc_fence_after();
       if (!warp_wait_bounded(&a2_empty[db], ((st >> 1) & 1) ^ 1, s_abort, err,
                              kRoleTrans | (st << 8)))
         break;
-      const uint32_t t_d1 = tmem + lane_base + kColD1 + db * 128;
-      const uint32_t t_a2 = tmem + lane_base + kColA2 + db * 64;
       for (int tt = 0; tt < ng; ++tt) {
-        uint32_t a[16], b[16];
-        tmem_ld16x2(t_d1 + 16 * tt, t_d1 + 16 * ng + 16 * tt, a, b);
+        uint32_t a[16];
+        tmem_ld16(t_d1 + 16 * tt, a);
         if (tt == ng - 1) {            // every read of this step's D1 is done
           tc_fence_before();
           mbar_arrive(&d1_empty[db]);
@@ -300,10 +325,10 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           float4 z;
-          z.x = (__uint_as_float(a[4 * u]) + __uint_as_float(b[4 * u])) * zscale;
-          z.y = (__uint_as_float(a[4 * u + 1]) + __uint_as_float(b[4 * u + 1])) * zscale;
-          z.z = (__uint_as_float(a[4 * u + 2]) + __uint_as_float(b[4 * u + 2])) * zscale;
-          z.w = (__uint_as_float(a[4 * u + 3]) + __uint_as_float(b[4 * u + 3])) * zscale;
+          z.x = __uint_as_float(a[4 * u]) * zscale;
+          z.y = __uint_as_float(a[4 * u + 1]) * zscale;
+          z.z = __uint_as_float(a[4 * u + 2]) * zscale;
+          z.w = __uint_as_float(a[4 * u + 3]) * zscale;
           *reinterpret_cast<float4 *>(tile + r * kTRow + 4 * u) = z;
         }
         __syncwarp();
@@ -321,7 +346,7 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
       tc_fence_before();
       mbar_arrive(&a2_full[db]);
     }
-  } else if (warp >= 12) {
+  } else if (warp >= 12 && warp < 16) {
     // ---------------------------------------------------------- epilogue
     const int q = warp & 3, lb = lane >> 4, j = lane & 15;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;

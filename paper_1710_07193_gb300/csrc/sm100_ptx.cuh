@@ -49,6 +49,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the same (returns at once).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase of `bar` with parity `parity` to complete.  Gives up
 // when another role raised *abort (returns false) or after kWaitLimitNs: then
 // the first such event of the launch is recorded in *err as `code` and
@@ -348,6 +361,17 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, uint32_t (
       "tcgen05.wait::ld.sync.aligned;"
       : DCTF_W16(a, 0), DCTF_W16(a, 16), DCTF_W16(b, 0), DCTF_W16(b, 16)
       : "r"(ta), "r"(tb)
+      : "memory");
+}
+
+// One 16-column load of this lane's row, waited for.
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&a)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : DCTF_W16(a, 0)
+      : "r"(ta)
       : "memory");
 }
 
