@@ -34,8 +34,8 @@
 //  epilogue  y[b][i][j] = (D2[i] + (D2[16 + i] + D2[32 + i])) 2^-(sZ + sA)
 //          + M[(i,j), 0] x0,
 //          the DC term kept out of the products and applied in FP32 as in
-//          the dense kernels; staged per block and written with 1 KB bulk
-//          copies.
+//          the dense kernels; each lane stores its block's column straight
+//          from registers.
 //
 // So a unit costs 3 + 2 r MMAs (r <= 4; 3 more per further group of four
 // terms), against the dense kernel's 3 x 256 x 256 MAC per block, and the
@@ -44,11 +44,11 @@
 // is read on the device.
 //
 // Roles (640 threads): warp 0 TMA producer (one 8 KB box per unit), warp 1
-// MMA issuer, warp 2 TMEM allocator, warps 4-7 converter (thread = row
-// (b, k): DC out, FP16 split, A1 to TMEM), warps 8-11 and 16-19 transposer
-// (even and odd steps), warps 12-15 epilogue.  The MMA issuer polls both
-// passes' queues and issues whichever is ready, so pass 1 runs ahead of the
-// transposers instead of waiting behind them.  Every wait is bounded
+// pass-1 MMA issuer, warp 2 TMEM allocator, warp 3 pass-2 MMA issuer, warps
+// 4-7 converter (thread = row (b, k): DC out, FP16 split, A1 to TMEM), warps
+// 8-11 and 16-19 transposer (even and odd steps), warps 12-15 epilogue.  The
+// two passes have their own issuing threads, so pass 1 runs ahead of the
+// transposers instead of waiting behind pass 2.  Every wait is bounded
 // (sm100_ptx.cuh).
 #include "sm100_ptx.cuh"
 
@@ -76,13 +76,11 @@ constexpr uint32_t kTmemCols = 512;
 // shared memory
 constexpr int kTRow = 20;                     // transposer tile row (floats)
 constexpr int kTBlk = 16 * kTRow + 16;        // per block: banks of a warp's 2 blocks disjoint
-constexpr int kOutBlk = 272;                  // staged block (floats): 1 KB + 64 B
 constexpr int kOffIn = 0;
 constexpr int kOffB1 = kOffIn + kStages * kUnitBytes;     // 16 KB pass-1 pieces
 constexpr int kOffB2 = kOffB1 + kKronPieceBytes / 2;      // 16 KB pass-2 pieces
 constexpr int kOffT = kOffB2 + kKronPieceBytes / 2;
-constexpr int kOffOut = kOffT + 2 * 4 * 2 * kTBlk * 4;   // two transposer sets
-constexpr int kOffMdc = kOffOut + 4 * 2 * 2 * kOutBlk * 4;
+constexpr int kOffMdc = kOffT + 2 * 4 * 2 * kTBlk * 4;   // two transposer sets
 constexpr int kOffDc = kOffMdc + kN2 * 4;
 constexpr int kOffBar = kOffDc + kDcRing * kUnit * 4;
 constexpr int kNumBars = 2 * kStages + 2 * kA1Bufs + 6 * 2 + 2 * kDcRing;
@@ -90,7 +88,6 @@ constexpr int kOffMisc = kOffBar + kNumBars * 8;
 constexpr int kSmem = kOffMisc + 16 + 1024;
 static_assert(kSmem <= 232448, "shared memory");
 static_assert(kOffB1 % 1024 == 0 && kOffB2 % 1024 == 0, "swizzle atoms");
-static_assert(kOffOut % 16 == 0 && (kOutBlk * 4) % 16 == 0, "bulk copy alignment");
 
 enum : uint32_t { kRoleProducer = 1, kRoleMma = 2, kRoleConv = 3, kRoleEpi = 4, kRoleDrain = 5,
                   kRoleTrans = 7 };
@@ -120,7 +117,6 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
   uint8_t *s_b1 = base + kOffB1;
   uint8_t *s_b2 = base + kOffB2;
   float *s_t = reinterpret_cast<float *>(base + kOffT);
-  float *s_out = reinterpret_cast<float *>(base + kOffOut);
   float *s_mdc = reinterpret_cast<float *>(base + kOffMdc);
   float *s_dc = reinterpret_cast<float *>(base + kOffDc);
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + kOffBar);
@@ -188,71 +184,59 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
     for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
       wait_drain(&full_in[k % kStages], (k / kStages) & 1, err, kRoleDrain);
   } else if (warp == 1 && lane == 0 && terms) {
-    // ---------------------------------------------------------- MMA issuer
-    // Two queues: pass 1 of step n1 (needs the unit's A1 and a free D1
-    // buffer) and pass 2 of step n2 < n1 (needs the step's A2 from a
-    // transposer and, at a unit's first group, a free D2).  Each round
-    // issues whatever is ready; a round without progress polls again, and
-    // after kWaitLimitNs without progress the launch gives up.
+    // ---------------------------------------------------------- pass-1 issuer
+    // D1 = x_hi B_lo^T + x_lo B_hi^T + x_hi B_hi^T for every step, in order
     uint64_t *last_bar = nullptr;
     uint32_t last_ph = 0;
-    int n1 = 0, n2 = 0;
-    uint64_t t_progress = globaltimer();
-    while (n2 < nsteps) {
-      bool progressed = false;
-      if (n1 < nsteps) {
-        const int k = n1 / NG, g = n1 % NG, ng = min(4, rank - 4 * g);
-        const int ab = k % kA1Bufs, db = n1 & 1;
-        if ((g != 0 || mbar_test_wait(&a1_full[ab], (k / kA1Bufs) & 1)) &&
-            mbar_test_wait(&d1_empty[db], ((n1 >> 1) & 1) ^ 1)) {
-          tc_fence_after();
-          const uint32_t t_a1 = tmem + kColA1 + ab * 16, t_d1 = tmem + kColD1 + db * 64;
-          const uint32_t idesc = idesc_f16(128, 16 * ng, false);
-          const uint64_t b_hi = desc_sw128(smem_u32(s_b1)) + 2 * g;              // K slot g
-          const uint64_t b_lo = desc_sw128(smem_u32(s_b1 + 16 * ng * 128)) + 2 * g;
-          mma_f16_ts(t_d1, t_a1, b_lo, idesc, 0u);          // x_hi B_lo
-          mma_f16_ts(t_d1, t_a1 + 8, b_hi, idesc, 1u);      // x_lo B_hi
-          mma_f16_ts(t_d1, t_a1, b_hi, idesc, 1u);          // x_hi B_hi
-          tc_commit(&d1_full[db]);
-          last_bar = &d1_full[db]; last_ph = (n1 >> 1) & 1;
-          if (g == NG - 1) tc_commit(&a1_empty[ab]);
-          ++n1;
-          progressed = true;
-        }
-      }
-      if (n2 < n1) {
-        const int k = n2 / NG, g = n2 % NG, ng = min(4, rank - 4 * g);
-        const int a2b = n2 & 1, d2b = k & 1;
-        if (mbar_test_wait(&a2_full[a2b], (n2 >> 1) & 1) &&
-            (g != 0 || mbar_test_wait(&d2_empty[d2b], ((k >> 1) & 1) ^ 1))) {
-          tc_fence_after();
-          const uint32_t t_a2 = tmem + kColA2 + a2b * 64, t_d2 = tmem + kColD2 + d2b * 48;
-          const uint64_t b2 = desc_sw128(smem_u32(s_b2 + g * 4096));   // K block g
-          for (int tt = 0; tt < ng; ++tt) {
-            const uint32_t acc = (g > 0 || tt > 0) ? 1u : 0u;
-            mma_f16_ts(t_d2, t_a2 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 32, false), acc);
-            mma_f16_ts(t_d2 + 32, t_a2 + 32 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 16, false),
-                       acc);
-          }
-          tc_commit(&a2_empty[a2b]);
-          last_bar = &a2_empty[a2b]; last_ph = (n2 >> 1) & 1;
-          if (g == NG - 1) tc_commit(&d2_full[d2b]);
-          ++n2;
-          progressed = true;
-        }
-      }
-      if (progressed) {
-        t_progress = globaltimer();
-      } else {
-        if (*s_abort) break;
-        if (globaltimer() - t_progress > kWaitLimitNs) {
-          atomicCAS(err, 0u, kRoleMma | (n2 << 8));
-          *s_abort = 1;
-          break;
-        }
-      }
+    for (int st = 0; st < nsteps; ++st) {
+      const int k = st / NG, g = st % NG, ng = min(4, rank - 4 * g);
+      const int ab = k % kA1Bufs, db = st & 1;
+      if (g == 0 && !wait_bounded(&a1_full[ab], (k / kA1Bufs) & 1, s_abort, err,
+                                  kRoleMma | (st << 8)))
+        break;
+      if (!wait_bounded(&d1_empty[db], ((st >> 1) & 1) ^ 1, s_abort, err, kRoleMma | (st << 8)))
+        break;
+      tc_fence_after();
+      const uint32_t t_a1 = tmem + kColA1 + ab * 16, t_d1 = tmem + kColD1 + db * 64;
+      const uint32_t idesc = idesc_f16(128, 16 * ng, false);
+      const uint64_t b_hi = desc_sw128(smem_u32(s_b1)) + 2 * g;              // K slot g
+      const uint64_t b_lo = desc_sw128(smem_u32(s_b1 + 16 * ng * 128)) + 2 * g;
+      mma_f16_ts(t_d1, t_a1, b_lo, idesc, 0u);          // x_hi B_lo
+      mma_f16_ts(t_d1, t_a1 + 8, b_hi, idesc, 1u);      // x_lo B_hi
+      mma_f16_ts(t_d1, t_a1, b_hi, idesc, 1u);          // x_hi B_hi
+      tc_commit(&d1_full[db]);
+      last_bar = &d1_full[db]; last_ph = (st >> 1) & 1;
+      if (g == NG - 1) tc_commit(&a1_empty[ab]);
     }
     // every MMA issued so far has completed once the last commit arrived
+    if (last_bar != nullptr) wait_drain(last_bar, last_ph, err, kRoleDrain);
+  } else if (warp == 3 && lane == 0 && terms) {
+    // ---------------------------------------------------------- pass-2 issuer
+    // per term, D2[0:32] (+)= Z_hi [A_hi | A_lo]^T, D2[32:48] (+)= Z_lo A_hi^T
+    uint64_t *last_bar = nullptr;
+    uint32_t last_ph = 0;
+    for (int st = 0; st < nsteps; ++st) {
+      const int k = st / NG, g = st % NG, ng = min(4, rank - 4 * g);
+      const int a2b = st & 1, d2b = k & 1;
+      if (!wait_bounded(&a2_full[a2b], (st >> 1) & 1, s_abort, err, kRoleMma | (st << 8)))
+        break;
+      if (g == 0 && !wait_bounded(&d2_empty[d2b], ((k >> 1) & 1) ^ 1, s_abort, err,
+                                  kRoleMma | (st << 8)))
+        break;
+      tc_fence_after();
+      const uint32_t t_a2 = tmem + kColA2 + a2b * 64, t_d2 = tmem + kColD2 + d2b * 48;
+      const uint64_t b2 = desc_sw128(smem_u32(s_b2 + g * 4096));   // K block g
+      for (int tt = 0; tt < ng; ++tt) {
+        const uint32_t acc = (g > 0 || tt > 0) ? 1u : 0u;
+        mma_f16_ts(t_d2, t_a2 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 32, false), acc);
+        mma_f16_ts(t_d2 + 32, t_a2 + 32 + 8 * tt, b2 + 2 * tt, idesc_f16(128, 16, false), acc);
+      }
+      tc_commit(&a2_empty[a2b]);
+      last_bar = &a2_empty[a2b]; last_ph = (st >> 1) & 1;
+      if (g == NG - 1) {
+        tc_commit(&d2_full[d2b]);
+      }
+    }
     if (last_bar != nullptr) wait_drain(last_bar, last_ph, err, kRoleDrain);
   } else if (warp >= 4 && warp < 8) {
     // ---------------------------------------------------------- converter
@@ -348,9 +332,15 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
     }
   } else if (warp >= 12 && warp < 16) {
     // ---------------------------------------------------------- epilogue
+    // lane (b, j) holds column j of block b's Y: it stores y[b][i][j] for
+    // every i straight from registers (a warp's store covers two 64-byte
+    // runs, whole sectors), with M[(i, j), 0] for the DC term in registers
     const int q = warp & 3, lb = lane >> 4, j = lane & 15;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const float oscale = __ldg(kscale + 1);
+    float mdc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) mdc[i] = s_mdc[i * 16 + j];
     for (int k = 0; k < my_units; ++k) {
       const int64_t unit = cta + (int64_t)k * G;
       float acc[16];
@@ -376,24 +366,13 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
         break;
       const float x0 = s_dc[slot * kUnit + 2 * q + lb];
       mbar_arrive(&dc_empty[slot]);
-      // this lane holds column j of its block's Y: stage the block row-major
-      const int o = k & 1;
-      float *buf = s_out + ((q * 2 + o) * 2) * kOutBlk;
-      if (lane == 0) bulk_wait_read<1>();   // the copies of unit k - 2 have read buffer o
-      __syncwarp();
+      const int64_t gb = unit * kUnit + 2 * q + lb;
+      if (gb < nblocks) {
+        float *dst = y + gb * kN2 + j;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) buf[lb * kOutBlk + i * 16 + j] = fmaf(s_mdc[i * 16 + j], x0, acc[i]);
-      fence_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        for (int b2 = 0; b2 < 2; ++b2) {
-          const int64_t gb = unit * kUnit + 2 * q + b2;
-          if (gb < nblocks) bulk_store(y + gb * kN2, buf + b2 * kOutBlk, kN2 * 4);
-        }
-        bulk_commit();
+        for (int i = 0; i < 16; ++i) __stcs(dst + i * 16, fmaf(mdc[i], x0, acc[i]));
       }
     }
-    if (lane == 0) bulk_wait<0>();
   }
 
   tc_fence_before();
