@@ -469,16 +469,22 @@ def run_workloads(lib, torch, reps: int):
         items.append((o, xi, yi, n))
         nb_total += n
     grp = lib.group_create(items)
+    # the fixed default (one CTA per SM, 128-row tiles, 3 stages x 2 slots),
+    # then the autotuner's choice
+    grp.set_config(0, 128, 3, 2)
+    t_default = graph_time_ms(torch, lambda s: grp.launch(stream=s), reps)
     grp.tune(reps=5)
     tg = graph_time_ms(torch, lambda s: grp.launch(stream=s), reps)
     ts = graph_time_ms(torch, lambda s: [lib.apply(o, xi, n, yi, stream=s) for o, xi, yi, n in items],
                        max(1, reps // 4))
-    grid, rows = grp.config()
+    grid, rows, stages, slots = grp.config()
     out["grouped_64_images"] = {"blocks": nb_total, "one_launch_us": 1e3 * tg,
+                                "default_config_us": 1e3 * t_default,
                                 "separate_launches_us": 1e3 * ts,
                                 "one_launch_blocks_per_s": nb_total / (tg / 1e3),
                                 "separate_blocks_per_s": nb_total / (ts / 1e3),
-                                "autotuned": {"ctas": grid, "tile_rows": rows},
+                                "autotuned": {"ctas": grid, "tile_rows": rows, "stages": stages,
+                                              "slots": slots},
                                 "one_launch_GBps": nb_total * BYTES_PER_BLOCK / (tg / 1e3) / 1e9}
     grp.destroy()
     # the same 64 images to filtered uint8 pixels in one persistent launch
@@ -554,12 +560,23 @@ def _r(v, k=4):
     return None if v is None else float(f"{v:.{k}g}")
 
 
-def headline_keys(simt, apply_mean_ms, pixels, planar, serving, e2e):
+def headline_keys(simt, apply_mean_ms, pixels, planar, serving, e2e, workloads=None):
     """The parts of the headline metric besides the tensor-core throughput,
     compact, for the end of the JSON line: the FP32 CUDA-core comparison
-    kernel, the fused pixel output, the image-plane layout, serving p50/p99
-    on both routes, and the end-to-end figure."""
+    kernel, the grouped and 16x16 workloads, the fused pixel output, the
+    image-plane layout, serving p50/p99 on both routes, and the end-to-end
+    figure."""
     out = {}
+    if workloads is not None:
+        g = workloads["grouped_64_images"]
+        out["grouped_64"] = {"us": _r(g["one_launch_us"]), "default_config_us": _r(g["default_config_us"]),
+                             "separate_us": _r(g["separate_launches_us"]),
+                             "hbm_frac": _r(g["one_launch_GBps"] * 1e3 / measured_peaks()[0], 3),
+                             "tuned": g["autotuned"]}
+        L = workloads["large_8192x8192_16x16"]
+        out["n16_8192"] = {k: _r(L[k]["us"]) for k in ("F16X3", "BF16X6", "TF32X3", "FP32_SIMT",
+                                                        "KRON_F16X3", "separable_9x9_KRON_F16X3",
+                                                        "separable_9x9_F16X3")}
     if simt is not None:
         out["fp32_simt"] = {"apply_us": _r(simt["apply_us"]), "f16x3_apply_us": _r(1e3 * apply_mean_ms),
                             "f16x3_speedup": _r(simt["apply_us"] / (1e3 * apply_mean_ms), 3),
@@ -893,7 +910,7 @@ def run_dctf(args):
         lib.apply(ops[0], x0, 65536, yp)
         torch.cuda.synchronize()
         line["cpu_baseline"]["parity"] = oracle_parity(job, x_host[:65536], yp.cpu().numpy())
-    line.update(headline_keys(simt, apply_mean, fused_pixels, planar, serving, e2e))
+    line.update(headline_keys(simt, apply_mean, fused_pixels, planar, serving, e2e, workloads))
     if rank == 0:
         print(json.dumps(line), flush=True)
     for o in ops:

@@ -300,14 +300,26 @@ dctf_status dctf_group_create(const dctf_group_item *items, int nitems,
  * work, so it can be captured in a CUDA graph and replayed. */
 dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream);
 
-/* Autotuner: time each candidate (CTA count x tile height) `reps` times on
- * this group (it really runs the group: no item may be in place; EINVAL
- * otherwise), keep the fastest for this group and cache it for its size
- * class.  Synchronises `stream`. */
+/* Autotuner: time each candidate (CTA count x tile height x shared-memory
+ * layout, i.e. input stages x operator slots) `reps` times on this group (it
+ * really runs the group: no item may be in place; EINVAL otherwise), keep
+ * the fastest for this group and cache it for its (device, kind, size
+ * class).  If the environment variable DCTF_TUNE_CACHE names a file, the
+ * cache is loaded from it when the first group is created and written back
+ * after each tuning.  Synchronises `stream`. */
 dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps);
 
-/* The launch parameters in use: CTA count and tile height (64 or 128). */
-dctf_status dctf_group_config(const dctf_group *g, int *grid, int *tile_rows);
+/* The launch parameters in use: CTA count, tile height (64 or 128), input
+ * stages and operator slots of the shared-memory layout.  Any output
+ * pointer may be NULL. */
+dctf_status dctf_group_config(const dctf_group *g, int *grid, int *tile_rows, int *stages,
+                              int *slots);
+
+/* Set the launch parameters by hand (grid 0: one CTA per SM).  The
+ * (stages, slots) layouts that exist: FP32 coefficient groups (3,2) (2,2)
+ * (4,1); int16 groups (4,2) (6,2) (8,1); pixel groups (4,2) (5,2) (6,1).
+ * EUNSUPPORTED for another layout; every layout gives the same bits. */
+dctf_status dctf_group_set_config(dctf_group *g, int grid, int tile_rows, int stages, int slots);
 
 /* Device status word of the group's launches (as dctf_operator_status). */
 dctf_status dctf_group_status(dctf_group *g, uint32_t *code, int clear);

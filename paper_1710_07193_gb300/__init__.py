@@ -61,7 +61,8 @@ _SIGS = {
     "dctf_group_create_pixels": (_i32, [_vp, _i32, _vp]),
     "dctf_group_launch": (_i32, [_vp, _vp]),
     "dctf_group_tune": (_i32, [_vp, _vp, _i32]),
-    "dctf_group_config": (_i32, [_vp, _vp, _vp]),
+    "dctf_group_config": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "dctf_group_set_config": (_i32, [_vp, _i32, _i32, _i32, _i32]),
     "dctf_group_status": (_i32, [_vp, _vp, _i32]),
     "dctf_group_destroy": (None, [_vp]),
     "dctf_apply_grouped": (_i32, [_vp, _i32, _i32, _vp]),
@@ -293,10 +294,14 @@ class Group:
     def tune(self, reps: int = 5, stream=None) -> None:
         _check(load().dctf_group_tune(self.handle, _stream(stream), reps))
 
-    def config(self) -> tuple[int, int]:
-        g, r = ctypes.c_int(0), ctypes.c_int(0)
-        _check(load().dctf_group_config(self.handle, ctypes.addressof(g), ctypes.addressof(r)))
-        return g.value, r.value
+    def config(self) -> tuple[int, int, int, int]:
+        """(CTAs, tile rows, input stages, operator slots) in use."""
+        v = [ctypes.c_int(0) for _ in range(4)]
+        _check(load().dctf_group_config(self.handle, *[ctypes.addressof(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def set_config(self, grid: int, tile_rows: int, stages: int, slots: int) -> None:
+        _check(load().dctf_group_set_config(self.handle, grid, tile_rows, stages, slots))
 
     def status(self, clear: bool = False) -> int:
         code = ctypes.c_uint32(0)

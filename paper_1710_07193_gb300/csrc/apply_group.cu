@@ -867,15 +867,35 @@ cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int he
                                                      err, s, pdl);
 }
 
+// Input stages and operator slots of the grouped launches, per variant
+// (the autotuner's third axis).  Shared memory bounds the product: an FP32
+// stage is 32 KB and a slot 17 KB, so one slot leaves room for a stage more.
+int group_variant_stages(int kind, int variant) {
+  static const int kStagesOf[3][kGroupVariants] = {{3, 2, 4}, {4, 6, 8}, {4, 5, 6}};
+  return kStagesOf[kind][variant];
+}
+int group_variant_slots(int, int variant) { return variant == 2 ? 1 : 2; }
+
 cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int64_t total_halves,
-                                      int grid, int max_take, uint32_t *err, cudaStream_t s) {
+                                      int grid, int max_take, uint32_t *err, cudaStream_t s,
+                                      int variant) {
   if (total_halves <= 0) return cudaSuccess;
   int64_t g = grid > 0 ? grid : 0;
   if (g > total_halves) g = total_halves;
   if (g < 1) g = 1;
   static const GroupItem kEmpty = {};
-  return launch_cfg<float, 4, 2, true, kModePixels>(d_items, kEmpty, nitems, total_halves, (int)g,
-                                                    max_take == 1 ? 1 : 2, 0, err, s, false);
+  const int take = max_take == 1 ? 1 : 2;
+  switch (variant) {
+    case 1:
+      return launch_cfg<float, 5, 2, true, kModePixels>(d_items, kEmpty, nitems, total_halves,
+                                                        (int)g, take, 0, err, s, false);
+    case 2:
+      return launch_cfg<float, 6, 1, true, kModePixels>(d_items, kEmpty, nitems, total_halves,
+                                                        (int)g, take, 0, err, s, false);
+    default:
+      return launch_cfg<float, 4, 2, true, kModePixels>(d_items, kEmpty, nitems, total_halves,
+                                                        (int)g, take, 0, err, s, false);
+  }
 }
 
 cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halves, int grid,
@@ -906,7 +926,7 @@ cudaError_t launch_apply_group_host(const GroupItem *d_items, int nitems, int64_
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,
-                               uint32_t *err, cudaStream_t s, bool pdl) {
+                               uint32_t *err, cudaStream_t s, bool pdl, int variant) {
   if (total_halves <= 0) return cudaSuccess;
   int64_t g = grid > 0 ? grid : 0;
   if (g > total_halves) g = total_halves;
@@ -919,10 +939,30 @@ cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single
                : launch_cfg<float, 4, 1, false>(nullptr, *single, 1, total_halves, (int)g, take, 1,
                                                err, s, pdl);
   }
-  return i16 ? launch_cfg<int16_t, 4, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take,
-                                              0, err, s, pdl)
-             : launch_cfg<float, 3, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take, 0,
-                                            err, s, pdl);
+  if (i16) {
+    switch (variant) {
+      case 1:
+        return launch_cfg<int16_t, 6, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take,
+                                               0, err, s, pdl);
+      case 2:
+        return launch_cfg<int16_t, 8, 1, true>(d_items, kEmpty, nitems, total_halves, (int)g, take,
+                                               0, err, s, pdl);
+      default:
+        return launch_cfg<int16_t, 4, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take,
+                                               0, err, s, pdl);
+    }
+  }
+  switch (variant) {
+    case 1:
+      return launch_cfg<float, 2, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take, 0,
+                                           err, s, pdl);
+    case 2:
+      return launch_cfg<float, 4, 1, true>(d_items, kEmpty, nitems, total_halves, (int)g, take, 0,
+                                           err, s, pdl);
+    default:
+      return launch_cfg<float, 3, 2, true>(d_items, kEmpty, nitems, total_halves, (int)g, take, 0,
+                                           err, s, pdl);
+  }
 }
 
 }  // namespace dctf

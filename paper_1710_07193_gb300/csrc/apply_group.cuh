@@ -70,11 +70,19 @@ cudaError_t launch_apply_planar(const dctf_operator *op, const float *in, int he
 cudaError_t launch_apply_host_direct(const GroupItem &single, int64_t total_halves, int grid,
                                      uint32_t *err, cudaStream_t s);
 
+// Grouped launches come in kGroupVariants shared-memory layouts (input
+// stages x operator slots), the autotuner's third axis; kind 0 = FP32
+// coefficients, 1 = int16, 2 = pixels.  Every variant gives the same bits.
+constexpr int kGroupVariants = 3;
+int group_variant_stages(int kind, int variant);
+int group_variant_slots(int kind, int variant);
+
 // Fused pixel output for many items (descriptors in global memory, each
 // filled as for launch_apply_pixels): one persistent launch, contiguous
-// schedule, two operator slots.
+// schedule.
 cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int64_t total_halves,
-                                      int grid, int max_take, uint32_t *err, cudaStream_t s);
+                                      int grid, int max_take, uint32_t *err, cudaStream_t s,
+                                      int variant = 0);
 
 // Host-direct grouped apply of int16 items (serving): each item's hin/hout
 // are mapped page-locked host buffers, its quantisation tables and operator
@@ -84,6 +92,6 @@ cudaError_t launch_apply_group_host(const GroupItem *d_items, int nitems, int64_
 
 cudaError_t launch_apply_group(const GroupItem *d_items, const GroupItem *single, int nitems,
                                int64_t total_halves, bool i16, int grid, int max_take,
-                               uint32_t *err, cudaStream_t s, bool pdl = false);
+                               uint32_t *err, cudaStream_t s, bool pdl = false, int variant = 0);
 
 }  // namespace dctf

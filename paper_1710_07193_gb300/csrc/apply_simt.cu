@@ -12,7 +12,8 @@
 // sums near one ulp of the output instead of growing with the DC magnitude.
 // For 8x8 blocks with FP32 input at full size, apply_simt_db_kernel runs the
 // same arithmetic with the next tile's loads overlapped (cp.async into a
-// second X buffer).
+// second X buffer); for 16x16 blocks, apply_simt16_db_kernel overlaps the
+// loads of the next chunk of M the same way.
 #include "dctf_internal.cuh"
 #include "sm100_ptx.cuh"
 
@@ -243,6 +244,132 @@ apply_simt_db_kernel(const float *__restrict__ M32, const float *__restrict__ Md
   }
 }
 
+// 16x16 blocks, FP32 input: M (256 KB) does not fit shared memory, so it
+// streams in 128 x 32 chunks, 16 per 32-block tile (two passes of 128
+// outputs, eight 32-input chunks each).  The chunk sequence is the same for
+// every tile, so the next chunk is always known: it is copied with cp.async
+// into the second of two chunk buffers while the current one computes.  Each
+// output still sums its inputs in order k = 0..255 with one FMA chain (the
+// DC term last), so the bits equal apply_simt_kernel's.
+struct Simt16Db {
+  static constexpr int N2 = 256, TB = 32, TN = 128, TK = 32, RB = 4, RN = 8;
+  static constexpr int TPB = TB / RB, TPN = TN / RN;     // 8 x 16 = 128 threads
+  static constexpr int kXP = N2 + 4, kMP = TK + 4, kYP = TN + 4;
+  static constexpr int kChunks = (N2 / TN) * (N2 / TK);  // 16 per tile
+  static constexpr int kXFloats = TB * kXP, kMFloats = TN * kMP, kYFloats = TB * kYP;
+  static constexpr size_t kSmem = (size_t)(kXFloats + 2 * kMFloats + kYFloats + TB) * 4;
+  static_assert(TPB * TPN == 128, "128 threads");
+};
+
+__global__ void __launch_bounds__(128)
+apply_simt16_db_kernel(const float *__restrict__ M32, const float *__restrict__ Mdc,
+                       const float *__restrict__ x, int64_t nblocks, float *y) {
+  using C = Simt16Db;
+  extern __shared__ __align__(16) float smem[];
+  float *Xs = smem;
+  float *Mb = Xs + C::kXFloats;                  // two chunk buffers
+  float *Ys = Mb + 2 * C::kMFloats;
+  float *x0s = Ys + C::kYFloats;
+  const int t = threadIdx.x, tb = t / C::TPN, tn = t % C::TPN;
+  const int64_t ntiles = (nblocks + C::TB - 1) / C::TB;
+  if ((int64_t)blockIdx.x >= ntiles) return;
+  // chunk c of a tile: outputs (c / 8) * 128.., inputs (c % 8) * 32..
+  auto issue_m = [&](int c, int buf) {
+    const int n0 = (c / (C::N2 / C::TK)) * C::TN, k0 = (c % (C::N2 / C::TK)) * C::TK;
+    float *dst = Mb + buf * C::kMFloats;
+    for (int idx = t; idx < C::TN * C::TK / 4; idx += 128) {
+      const int r = idx / (C::TK / 4), c4 = idx % (C::TK / 4);
+      cp_async_16(smem_u32(dst + r * C::kMP + 4 * c4), M32 + (size_t)(n0 + r) * C::N2 + k0 + 4 * c4,
+                  16u);
+    }
+    cp_async_commit();
+  };
+  int cnt = 0;                                   // chunks computed so far by this CTA
+  issue_m(0, 0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t b0 = tile * C::TB;
+    __syncthreads();   // the previous tile's readers of Xs / Ys are done
+    for (int idx = t; idx < C::TB * C::N2 / 4; idx += 128) {
+      const int r = idx / (C::N2 / 4), c4 = idx % (C::N2 / 4);
+      const int64_t b = b0 + r;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b < nblocks) v = __ldg(reinterpret_cast<const float4 *>(x + b * C::N2) + c4);
+      if (c4 == 0) { x0s[r] = v.x; v.x = 0.f; }
+      *reinterpret_cast<float4 *>(&Xs[r * C::kXP + 4 * c4]) = v;
+    }
+    for (int n0 = 0; n0 < C::N2; n0 += C::TN) {
+      float acc[C::RB][C::RN];
+#pragma unroll
+      for (int i = 0; i < C::RB; ++i)
+#pragma unroll
+        for (int j = 0; j < C::RN; ++j) acc[i][j] = 0.f;
+      for (int k0 = 0; k0 < C::N2; k0 += C::TK, ++cnt) {
+        __syncthreads();   // every thread is done with the buffer of chunk cnt - 1
+        issue_m((cnt + 1) % C::kChunks, (cnt + 1) & 1);
+        cp_async_wait_group<1>();   // this thread's copies of chunk cnt have landed
+        __syncthreads();            // and every other thread's
+        const float *Ms = Mb + (cnt & 1) * C::kMFloats;
+#pragma unroll 2
+        for (int k4 = 0; k4 < C::TK; k4 += 4) {
+          float4 xa[C::RB], ma[C::RN];
+#pragma unroll
+          for (int i = 0; i < C::RB; ++i)
+            xa[i] = *reinterpret_cast<const float4 *>(&Xs[(tb + C::TPB * i) * C::kXP + k0 + k4]);
+#pragma unroll
+          for (int j = 0; j < C::RN; ++j)
+            ma[j] = *reinterpret_cast<const float4 *>(&Ms[(tn + C::TPN * j) * C::kMP + k4]);
+#pragma unroll
+          for (int i = 0; i < C::RB; ++i)
+#pragma unroll
+            for (int j = 0; j < C::RN; ++j) {
+              acc[i][j] = fmaf(xa[i].x, ma[j].x, acc[i][j]);
+              acc[i][j] = fmaf(xa[i].y, ma[j].y, acc[i][j]);
+              acc[i][j] = fmaf(xa[i].z, ma[j].z, acc[i][j]);
+              acc[i][j] = fmaf(xa[i].w, ma[j].w, acc[i][j]);
+            }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < C::RN; ++j) {
+        const float md = __ldg(Mdc + n0 + tn + C::TPN * j);
+#pragma unroll
+        for (int i = 0; i < C::RB; ++i) acc[i][j] = fmaf(md, x0s[tb + C::TPB * i], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < C::RB; ++i)
+#pragma unroll
+        for (int j = 0; j < C::RN; ++j) Ys[(tb + C::TPB * i) * C::kYP + tn + C::TPN * j] = acc[i][j];
+      __syncthreads();
+      for (int idx = t; idx < C::TB * C::TN / 4; idx += 128) {
+        const int r = idx / (C::TN / 4), c4 = idx % (C::TN / 4);
+        const int64_t b = b0 + r;
+        if (b < nblocks)
+          *reinterpret_cast<float4 *>(y + b * C::N2 + n0 + 4 * c4) =
+              *reinterpret_cast<const float4 *>(&Ys[r * C::kYP + 4 * c4]);
+      }
+    }
+  }
+  cp_async_wait_group<0>();   // the prefetch of a chunk no tile uses
+}
+
+cudaError_t launch_simt16_db(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
+                             cudaStream_t s) {
+  using C = Simt16Db;
+  cudaError_t e = cudaFuncSetAttribute(apply_simt16_db_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_simt16_db_kernel, 128, C::kSmem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t ntiles = (nblocks + C::TB - 1) / C::TB;
+  int64_t grid = (int64_t)per_sm * sm_count(op->device);
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  apply_simt16_db_kernel<<<(unsigned)grid, 128, C::kSmem, s>>>(op->d_M32, op->d_Mdc, x, nblocks, y);
+  return cudaGetLastError();
+}
+
 template <int N2, int TB, int RB, int RN>
 cudaError_t launch_db(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
                       cudaStream_t s) {
@@ -299,7 +426,12 @@ cudaError_t dispatch(const dctf_operator *op, const Tin *x, int64_t nblocks, flo
         return launch_db<64, 128, 8, 8>(op, reinterpret_cast<const float *>(x), nblocks, y, s);
       else
         return launch_cfg<Tin, 64, 128, 64, 64, 8, 8>(op, x, nblocks, y, s);
-    case 16: return launch_cfg<Tin, 256, 32, 128, 64, 4, 8>(op, x, nblocks, y, s);
+    case 16:
+      // FP32 input: the M chunks double-buffered (same bits)
+      if constexpr (sizeof(Tin) == 4)
+        return launch_simt16_db(op, reinterpret_cast<const float *>(x), nblocks, y, s);
+      else
+        return launch_cfg<Tin, 256, 32, 128, 64, 4, 8>(op, x, nblocks, y, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -8,13 +8,20 @@
 // descriptors; launching it is then a single kernel launch with no host work,
 // so it can be captured in a CUDA graph and replayed.
 //
-// Autotuner.  Two launch parameters matter for uneven batches: the number of
-// persistent CTAs and the tile height (128-row tiles, or 64-row tiles that
-// balance small items better).  dctf_group_tune times every candidate on the
-// group itself (CUDA events, median of `reps`) and keeps the fastest; the
-// choice is also cached per (I/O type, size class) and used as the default
-// for later groups of that class.
+// Autotuner.  Three launch parameters matter for uneven batches: the number
+// of persistent CTAs, the tile height (128-row tiles, or 64-row tiles that
+// balance small items better) and the shared-memory layout (input stages x
+// operator slots: more stages keep more loads in flight, two slots let
+// operator switches overlap the previous item's tiles).  dctf_group_tune
+// times every candidate on the group itself (CUDA events, median of `reps`)
+// and keeps the fastest; the choice is also cached per (device, I/O type,
+// size class) and used as the default for later groups of that class.  With
+// DCTF_TUNE_CACHE naming a file, the cache is read from it at the first
+// group and written back after every tuning, so later processes start from
+// the tuned choice.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -33,6 +40,7 @@ struct dctf_group {
   uint32_t *d_err;
   int grid;        // CTAs (0: one per SM)
   int max_take;    // 2: 128-row tiles, 1: 64-row tiles
+  int variant;     // shared-memory layout (stages x slots), 0..kGroupVariants-1
   bool in_place;   // some item filters in place (tuning would re-filter it)
 };
 
@@ -40,17 +48,51 @@ namespace dctf {
 namespace {
 
 struct TuneKey {
+  int sms;          // the device, by its SM count (one process may see several kinds)
   int kind;         // 0: FP32 coefficients, 1: int16, 2: pixels
   int size_class;   // floor(log2(total halves))
   bool operator<(const TuneKey &o) const {
+    if (sms != o.sms) return sms < o.sms;
     return kind != o.kind ? kind < o.kind : size_class < o.size_class;
   }
 };
 int kind_of(const dctf_group *g) { return g->pixels ? 2 : g->i16 ? 1 : 0; }
-struct TuneVal { int grid_num, grid_den, max_take; };
+struct TuneVal { int grid_num, grid_den, max_take, variant; };
 
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
+bool g_tune_loaded = false;
+
+// The persistent cache file (DCTF_TUNE_CACHE), one line per entry:
+// "sms kind size_class grid_num grid_den max_take variant".  Unreadable or
+// malformed lines are ignored; callers hold g_tune_mu.
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = getenv("DCTF_TUNE_CACHE");
+  if (path == nullptr || *path == 0) return;
+  FILE *f = fopen(path, "r");
+  if (f == nullptr) return;
+  TuneKey k;
+  TuneVal v;
+  while (fscanf(f, "%d %d %d %d %d %d %d", &k.sms, &k.kind, &k.size_class, &v.grid_num,
+                &v.grid_den, &v.max_take, &v.variant) == 7) {
+    if (k.kind >= 0 && k.kind <= 2 && v.grid_num > 0 && v.grid_den > 0 && v.grid_num <= v.grid_den &&
+        (v.max_take == 1 || v.max_take == 2) && v.variant >= 0 && v.variant < kGroupVariants)
+      g_tune_cache[k] = v;
+  }
+  fclose(f);
+}
+void tune_cache_save() {
+  const char *path = getenv("DCTF_TUNE_CACHE");
+  if (path == nullptr || *path == 0) return;
+  FILE *f = fopen(path, "w");
+  if (f == nullptr) return;
+  for (const auto &kv : g_tune_cache)
+    fprintf(f, "%d %d %d %d %d %d %d\n", kv.first.sms, kv.first.kind, kv.first.size_class,
+            kv.second.grid_num, kv.second.grid_den, kv.second.max_take, kv.second.variant);
+  fclose(f);
+}
 
 int size_class(int64_t halves) {
   int c = 0;
@@ -162,12 +204,12 @@ dctf_status fill_pixel_items(const dctf_pixel_item *items, int nitems,
   return DCTF_OK;
 }
 
-cudaError_t launch(const dctf_group *g, int grid, int max_take, cudaStream_t s) {
+cudaError_t launch(const dctf_group *g, int grid, int max_take, int variant, cudaStream_t s) {
   if (g->pixels)
     return launch_apply_group_pixels(g->d_items, g->nitems, g->total_halves, grid, max_take,
-                                     g->d_err, s);
+                                     g->d_err, s, variant);
   return launch_apply_group(g->d_items, nullptr, g->nitems, g->total_halves, g->i16, grid,
-                            max_take, g->d_err, s);
+                            max_take, g->d_err, s, false, variant);
 }
 
 // Uploads the descriptors and picks the launch parameters (the autotuner's
@@ -198,14 +240,17 @@ dctf_status make_group(const std::vector<GroupItem> &host, int nitems, int64_t t
   }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tune_cache.find(TuneKey{kind_of(g), size_class(total)});
+    tune_cache_load();
     const int sms = sm_count(g->device);
+    auto it = g_tune_cache.find(TuneKey{sms, kind_of(g), size_class(total)});
     if (it != g_tune_cache.end()) {
       g->grid = std::max(1, sms * it->second.grid_num / it->second.grid_den);
       g->max_take = it->second.max_take;
+      g->variant = it->second.variant;
     } else {
       g->grid = 0;
       g->max_take = 2;
+      g->variant = 0;
     }
   }
   *out = g;
@@ -251,7 +296,7 @@ dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream) {
   if (g == nullptr) return set_error(DCTF_EINVAL, "group is NULL");
   if (g->total_halves == 0) return DCTF_OK;
   int grid = g->grid > 0 ? g->grid : sm_count(g->device);
-  cudaError_t e = launch(g, grid, g->max_take, stream);
+  cudaError_t e = launch(g, grid, g->max_take, g->variant, stream);
   if (e != cudaSuccess) return cuda_error(e, "grouped apply launch");
   return DCTF_OK;
 }
@@ -268,14 +313,15 @@ dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps) {
   DCTF_CUDA(cudaEventCreate(&e0));
   DCTF_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  TuneVal best_v{1, 1, 2};
+  TuneVal best_v{1, 1, 2, 0};
+  for (int v = 0; v < kGroupVariants; ++v)
   for (const auto &f : kFrac) {
     for (int take = 2; take >= 1; --take) {
       const int grid = std::max(1, sms * f[0] / f[1]);
       std::vector<float> ts;
       for (int r = 0; r < reps + 1; ++r) {
         cudaEventRecord(e0, stream);
-        cudaError_t e = launch(g, grid, take, stream);
+        cudaError_t e = launch(g, grid, take, v, stream);
         cudaEventRecord(e1, stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
@@ -289,22 +335,43 @@ dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps) {
       }
       std::sort(ts.begin(), ts.end());
       const float med = ts[ts.size() / 2];
-      if (med < best) { best = med; best_v = TuneVal{f[0], f[1], take}; }
+      if (med < best) { best = med; best_v = TuneVal{f[0], f[1], take, v}; }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g->grid = std::max(1, sms * best_v.grid_num / best_v.grid_den);
   g->max_take = best_v.max_take;
+  g->variant = best_v.variant;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune_cache[TuneKey{kind_of(g), size_class(g->total_halves)}] = best_v;
+  tune_cache_load();
+  g_tune_cache[TuneKey{sms, kind_of(g), size_class(g->total_halves)}] = best_v;
+  tune_cache_save();
   return DCTF_OK;
 }
 
-dctf_status dctf_group_config(const dctf_group *g, int *grid, int *tile_rows) {
+dctf_status dctf_group_config(const dctf_group *g, int *grid, int *tile_rows, int *stages,
+                              int *slots) {
   if (g == nullptr) return set_error(DCTF_EINVAL, "group is NULL");
   if (grid) *grid = g->grid > 0 ? g->grid : sm_count(g->device);
   if (tile_rows) *tile_rows = 64 * g->max_take;
+  if (stages) *stages = group_variant_stages(kind_of(g), g->variant);
+  if (slots) *slots = group_variant_slots(kind_of(g), g->variant);
+  return DCTF_OK;
+}
+
+dctf_status dctf_group_set_config(dctf_group *g, int grid, int tile_rows, int stages, int slots) {
+  if (g == nullptr) return set_error(DCTF_EINVAL, "group is NULL");
+  if (grid < 0 || (tile_rows != 64 && tile_rows != 128))
+    return set_error(DCTF_EINVAL, "grid must be >= 0 and tile_rows 64 or 128");
+  int v = -1;
+  for (int k = 0; k < kGroupVariants; ++k)
+    if (group_variant_stages(kind_of(g), k) == stages && group_variant_slots(kind_of(g), k) == slots)
+      v = k;
+  if (v < 0) return set_error(DCTF_EUNSUPPORTED, "no layout with %d stages and %d slots", stages, slots);
+  g->grid = grid;
+  g->max_take = tile_rows / 64;
+  g->variant = v;
   return DCTF_OK;
 }
 

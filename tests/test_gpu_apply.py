@@ -92,6 +92,27 @@ def test_simt_tile_configs_agree(dctf, ragged_source):
     op.release()
 
 
+@pytest.mark.parametrize("nb", [1, 31, 33, 1000, 40000])
+def test_simt16_double_buffered_same_bits(dctf, n16_source, nb):
+    """16x16 FP32 CUDA cores: the kernel that streams M's chunks double-
+    buffered (FP32 input) gives the same bits as the single-buffered kernel
+    (taken by the FP64-input entry point, fed the same values), and both meet
+    the oracle."""
+    blocks, x = n16_source
+    x, blocks = x[:nb], blocks[:nb]
+    w, a = datagen.large_mask(), (4, 4)
+    op = dctf.build_operator(w, a, 16, dctf.REPLICATE)
+    y_db = run(dctf, op, x, dctf.FP32_SIMT)
+    xd = torch.from_numpy(x.astype(np.float64)).cuda()
+    yd = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+    dctf.apply_f64in(op, xd, nb, yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(y_db, yd.cpu().numpy().astype(np.float64))
+    check(y_db, x, blocks, w, a, 16, oracle.REPLICATE)
+    assert np.array_equal(run(dctf, op, x, dctf.FP32_SIMT, inplace=True), y_db)
+    op.release()
+
+
 def test_small_workload_fp64_coefficients(dctf):
     """256x256, 3x3 Gaussian sigma=1, zero padding, FP64 coefficients in."""
     job = datagen.small_job()

@@ -68,8 +68,8 @@ def test_group_graph_replay_and_tune(dctf, small_batch):
     torch.cuda.synchronize()
     for (_, _, yd, _), (job, blocks, x) in zip(items, refs):
         check_item(yd.cpu().numpy().astype(np.float64), job, blocks, x)
-    grid, rows = g.config()
-    assert grid >= 1 and rows in (64, 128)
+    grid, rows, stages, slots = g.config()
+    assert grid >= 1 and rows in (64, 128) and (stages, slots) in ((3, 2), (2, 2), (4, 1))
     for _, _, yd, _ in items:
         yd.fill_(float("nan"))
     s = torch.cuda.Stream()
@@ -175,3 +175,103 @@ def test_group_int16_dequant_requant(dctf):
         # the tables are not interchangeable: the swapped order disagrees
         _, v_swapped = oracle.serve_blocks(qin, qo, m, q)
         assert oracle.int16_compare(v_swapped, got, BAND)["mismatch"] > 0
+
+
+def test_group_layouts_same_bits(dctf, small_batch):
+    """Every shared-memory layout the tuner chooses from (input stages x
+    operator slots), with either tile height, gives the same bits as the
+    default launch, for FP32 coefficient groups and pixel groups."""
+    items, refs = make_items(dctf, small_batch)
+    g = dctf.group_create(items)
+    g.launch()
+    torch.cuda.synchronize()
+    want = [yd.cpu().numpy().copy() for _, _, yd, _ in items]
+    imgs = [torch.zeros(job.image.shape, dtype=torch.uint8, device="cuda") for job, _, _ in refs]
+    gp = dctf.group_create_pixels([(op, xd, job.image.shape[0], job.image.shape[1], im)
+                                   for (op, xd, _, _), (job, _, _), im in zip(items, refs, imgs)])
+    gp.launch()
+    torch.cuda.synchronize()
+    want_px = [im.cpu().numpy().copy() for im in imgs]
+    for grp, layouts, outs, ref in ((g, ((3, 2), (2, 2), (4, 1)), [it[2] for it in items], want),
+                                    (gp, ((4, 2), (5, 2), (6, 1)), imgs, want_px)):
+        for stages, slots in layouts:
+            for rows in (128, 64):
+                grp.set_config(57, rows, stages, slots)
+                assert grp.config() == (57, rows, stages, slots)
+                for o in outs:
+                    o.zero_()
+                grp.launch()
+                torch.cuda.synchronize()
+                for o, w in zip(outs, ref):
+                    assert np.array_equal(o.cpu().numpy(), w)
+        with pytest.raises(dctf.DctfError) as e:
+            grp.set_config(0, 128, 7, 2)
+        assert e.value.status == 6
+        assert grp.status() == 0
+    g.destroy()
+    gp.destroy()
+
+
+def test_group_int16_layouts_same_bits(dctf):
+    img = datagen.synthetic_image(256, 320, datagen.rng(98, 77, 0))
+    qin, q = quantised_plane(img, 2)
+    w, a, bnd = datagen.serving_mask(5)
+    op = dctf.build_operator(w, a, 8, bnd)
+    xd = torch.from_numpy(qin).cuda()
+    qd = torch.from_numpy(q.ravel().astype(np.int16)).cuda()
+    outs = [torch.zeros_like(xd) for _ in range(3)]
+    g = dctf.group_create([(op, xd, o, qin.shape[0] // (k + 1), qd, qd) for k, o in enumerate(outs)],
+                          io=dctf.IO_I16)
+    res = []
+    for stages, slots in ((4, 2), (6, 2), (8, 1)):
+        g.set_config(0, 128, stages, slots)
+        for o in outs:
+            o.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        res.append([o.cpu().numpy().copy() for o in outs])
+    for r in res[1:]:
+        for a_, b_ in zip(res[0], r):
+            assert np.array_equal(a_, b_)
+    _, v = oracle.serve_blocks(qin, q, oracle.build_M(w, a, 8, bnd), q)
+    assert oracle.int16_compare(v, res[0][0], BAND)["mismatch"] == 0
+    g.destroy()
+
+
+_TUNE_CHILD = """
+import sys, json
+sys.path.insert(0, sys.argv[1])
+import numpy as np, torch
+import datagen, oracle
+import paper_1710_07193_gb300 as dctf
+dctf.load()
+jobs = datagen.grouped_jobs(count=6, scale=0.2)
+items = []
+for j in jobs:
+    x = oracle.dct2_blocks(oracle.image_to_blocks(j.image, 8)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    items.append((dctf.build_operator(j.mask, j.anchor, 8, j.boundary), xd, torch.empty_like(xd),
+                  x.shape[0]))
+g = dctf.group_create(items)
+if sys.argv[2] == "tune":
+    g.tune(reps=2)
+print(json.dumps(list(g.config())))
+"""
+
+
+def test_tune_cache_persists_across_processes(dctf, tmp_path):
+    """DCTF_TUNE_CACHE: a tuning is written to the file, and a new process
+    creating a group of the same size class starts from that choice."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DCTF_TUNE_CACHE=str(tmp_path / "tune.txt"))
+    run = lambda mode: json.loads(subprocess.run(
+        [sys.executable, "-c", _TUNE_CHILD, root, mode], env=env, capture_output=True, text=True,
+        timeout=300, check=True).stdout.strip().splitlines()[-1])
+    tuned = run("tune")
+    lines = (tmp_path / "tune.txt").read_text().split("\n")
+    assert any(len(ln.split()) == 7 for ln in lines)
+    assert run("none") == tuned
