@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--serving-only", action="store_true",
                    help="run only the serving phase (rank 0) and print its JSON; not a bench "
                         "line")
+    p.add_argument("--only", choices=["small", "grouped", "large"], default=None,
+                   help="with --workloads-only: run one of the workloads (for profiling it)")
     p.add_argument("--workloads-only", action="store_true",
                    help="run only the small / grouped / 16x16 workloads (rank 0) and print "
                         "their JSON; not a bench line (for profiling them)")
@@ -434,10 +436,13 @@ def graph_time_ms(torch, fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def run_workloads(lib, torch, reps: int):
-    """The other four workloads, timed on the device (CUDA graphs)."""
+def run_workloads(lib, torch, reps: int, only=None):
+    """The other four workloads, timed on the device (CUDA graphs); `only`
+    selects one of them ("small", "grouped", "large")."""
     dev = torch.device("cuda")
     out = {}
+    if only not in (None, "small"):
+        return run_workloads_rest(lib, torch, reps, out, only)
     # small: 256x256, 3x3 Gaussian sigma=1, zero padding, FP64 coefficients in
     job = datagen.small_job()
     img = torch.from_numpy(job.image).to(dev)
@@ -455,6 +460,23 @@ def run_workloads(lib, torch, reps: int):
     out["small_256x256"] = {"blocks": nb, "fp64_in_us": 1e3 * t64, "f16x3_fp32_in_us": 1e3 * t16,
                             "operator_build_us": 1e3 * tb}
     op.release()
+    if only == "small":
+        return out
+    return run_workloads_rest(lib, torch, reps, out, None)
+
+
+def run_workloads_rest(lib, torch, reps: int, out: dict, only):
+    """The grouped and 16x16 workloads (both, or the one `only` names)."""
+    dev = torch.device("cuda")
+    if only != "large":
+        run_grouped(lib, torch, reps, out)
+    if only != "grouped":
+        run_large(lib, torch, reps, out)
+    return out
+
+
+def run_grouped(lib, torch, reps: int, out: dict):
+    dev = torch.device("cuda")
     # grouped: 64 images of seeded sizes, one mask and boundary each
     jobs = datagen.grouped_jobs()
     items, keep, nb_total = [], [], 0
@@ -501,6 +523,10 @@ def run_workloads(lib, torch, reps: int):
     for o, *_ in items:
         o.release()
     del items
+
+
+def run_large(lib, torch, reps: int, out: dict):
+    dev = torch.device("cuda")
     # large: 8192x8192, 16x16 blocks, perturbed 9x9 Gaussian, replication
     job = datagen.large_job()
     img = torch.from_numpy(job.image).to(dev)
@@ -551,7 +577,6 @@ def run_workloads(lib, torch, reps: int):
     res["separable_9x9_KRON_FP32"]["terms"] = res["separable_9x9_KRON_F16X3"]["terms"] = op.kron_rank()
     out["large_8192x8192_16x16"] = res
     op.release()
-    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -615,7 +640,7 @@ def run_dctf(args):
     lib.load()
     if args.workloads_only:
         if rank == 0:
-            print(json.dumps({"workloads": run_workloads(lib, torch, 40)}), flush=True)
+            print(json.dumps({"workloads": run_workloads(lib, torch, 40, args.only)}), flush=True)
         return
     if args.serving_only:
         if rank == 0:
