@@ -46,7 +46,7 @@ GRAPH_STEPS = 200       # steps per captured graph; the timed loop replays sever
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "adbff8365050c3efec30d9026f5030be3ab3b926": 131911578,
+    "7105c3db73e5b065cc12bee4183b2c81b1a971ea": 131912141,
 }
 
 
@@ -596,7 +596,7 @@ def headline_keys(simt, apply_mean_ms, pixels, planar, serving, e2e, workloads=N
         g = workloads["grouped_64_images"]
         out["grouped_64"] = {"us": _r(g["one_launch_us"]), "default_config_us": _r(g["default_config_us"]),
                              "separate_us": _r(g["separate_launches_us"]),
-                             "hbm_frac": _r(g["one_launch_GBps"] * 1e3 / measured_peaks()[0], 3),
+                             "hbm_frac": _r(g["one_launch_GBps"] / measured_peaks()[0], 3),
                              "tuned": g["autotuned"]}
         L = workloads["large_8192x8192_16x16"]
         out["n16_8192"] = {k: _r(L[k]["us"]) for k in ("F16X3", "BF16X6", "TF32X3", "FP32_SIMT",
