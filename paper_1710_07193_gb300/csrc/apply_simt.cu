@@ -250,26 +250,28 @@ apply_simt_db_kernel(const float *__restrict__ M32, const float *__restrict__ Md
 // every tile, so the next chunk is always known: it is copied with cp.async
 // into the second of two chunk buffers while the current one computes.  Each
 // output still sums its inputs in order k = 0..255 with one FMA chain (the
-// DC term last), so the bits equal apply_simt_kernel's.
+// DC term last), so the bits equal apply_simt_kernel's.  Outputs go straight
+// from registers to global memory (for each of a thread's outputs, the 16
+// threads of its block row store 64 contiguous bytes), so no staging buffer:
+// 70 KB of shared memory a CTA, three CTAs per SM.
 struct Simt16Db {
   static constexpr int N2 = 256, TB = 32, TN = 128, TK = 32, RB = 4, RN = 8;
   static constexpr int TPB = TB / RB, TPN = TN / RN;     // 8 x 16 = 128 threads
-  static constexpr int kXP = N2 + 4, kMP = TK + 4, kYP = TN + 4;
+  static constexpr int kXP = N2 + 4, kMP = TK + 4;
   static constexpr int kChunks = (N2 / TN) * (N2 / TK);  // 16 per tile
-  static constexpr int kXFloats = TB * kXP, kMFloats = TN * kMP, kYFloats = TB * kYP;
-  static constexpr size_t kSmem = (size_t)(kXFloats + 2 * kMFloats + kYFloats + TB) * 4;
+  static constexpr int kXFloats = TB * kXP, kMFloats = TN * kMP;
+  static constexpr size_t kSmem = (size_t)(kXFloats + 2 * kMFloats + TB) * 4;
   static_assert(TPB * TPN == 128, "128 threads");
 };
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 3)
 apply_simt16_db_kernel(const float *__restrict__ M32, const float *__restrict__ Mdc,
                        const float *__restrict__ x, int64_t nblocks, float *y) {
   using C = Simt16Db;
   extern __shared__ __align__(16) float smem[];
   float *Xs = smem;
   float *Mb = Xs + C::kXFloats;                  // two chunk buffers
-  float *Ys = Mb + 2 * C::kMFloats;
-  float *x0s = Ys + C::kYFloats;
+  float *x0s = Mb + 2 * C::kMFloats;
   const int t = threadIdx.x, tb = t / C::TPN, tn = t % C::TPN;
   const int64_t ntiles = (nblocks + C::TB - 1) / C::TB;
   if ((int64_t)blockIdx.x >= ntiles) return;
@@ -335,17 +337,14 @@ apply_simt16_db_kernel(const float *__restrict__ M32, const float *__restrict__ 
 #pragma unroll
         for (int i = 0; i < C::RB; ++i) acc[i][j] = fmaf(md, x0s[tb + C::TPB * i], acc[i][j]);
       }
+      // in place is safe: the whole tile's input is in Xs already
 #pragma unroll
-      for (int i = 0; i < C::RB; ++i)
+      for (int i = 0; i < C::RB; ++i) {
+        const int64_t b = b0 + tb + C::TPB * i;
+        if (b < nblocks) {
 #pragma unroll
-        for (int j = 0; j < C::RN; ++j) Ys[(tb + C::TPB * i) * C::kYP + tn + C::TPN * j] = acc[i][j];
-      __syncthreads();
-      for (int idx = t; idx < C::TB * C::TN / 4; idx += 128) {
-        const int r = idx / (C::TN / 4), c4 = idx % (C::TN / 4);
-        const int64_t b = b0 + r;
-        if (b < nblocks)
-          *reinterpret_cast<float4 *>(y + b * C::N2 + n0 + 4 * c4) =
-              *reinterpret_cast<const float4 *>(&Ys[r * C::kYP + 4 * c4]);
+          for (int j = 0; j < C::RN; ++j) y[b * C::N2 + n0 + tn + C::TPN * j] = acc[i][j];
+        }
       }
     }
   }
