@@ -19,13 +19,7 @@
 // Tensor-core FP32 accumulation truncates, so the order matters: per K half
 // of 128 inputs, each with its own accumulator, the correction products go
 // in first (while the accumulator is small), the main product x_0 m_0 last;
-// the epilogue adds the two halves with round-to-nearest.  The two-piece
-// splits with CTA pairs (F16X3, BF16X3) are "stacked" instead: M's hi and lo
-// rows sit next to each other in shared memory, so per K step x_hi
-// [M_hi | M_lo]^T is one MMA of N = 256 and x_lo M_hi^T one of N = 128 (4
-// MMAs per chunk where the per-product form issues 6: the same tensor work
-// in fewer, wider instructions), each product summed over all of K in its
-// own accumulator columns, added in the epilogue.
+// the epilogue adds the two halves with round-to-nearest.
 //
 // What 16x16 changes against the 8x8 kernel (apply_group.cu) is size: M is
 // 256 x 256, its pieces 256-512 KB, more than one SM's shared memory, and a
@@ -65,37 +59,35 @@ using namespace ptx;
 // kImgPieces  : pieces stacked per chunk in the operator's piece image
 // kTf32       : TF32 pieces (kind::tf32), else 16-bit pieces (kind::f16)
 // kOut, kDBufs: outputs per CTA, accumulator sets (tiles) in TMEM
-// kCorr       : correction products; corr_x(j), corr_m(j) their pieces (not
-//               stacked)
-// kStacked    : two pieces, hi and lo of M adjacent in shared memory, so per
-//               K step x_hi [M_hi | M_lo]^T is ONE MMA of N = 2 kOut and
-//               x_lo M_hi^T one of N = kOut: 4 MMAs per 32-input chunk
-//               instead of 6, each product in its own accumulator columns
-//               (main | x_hi M_lo | x_lo M_hi, 3 kOut columns) over all of K
+// kCorr       : correction products; corr_x(j), corr_m(j) their pieces
 struct SplitF16x3 {
-  static constexpr int kPieces = 2, kImgPieces = 2, kOut = 128, kDBufs = 1;
-  static constexpr bool kTf32 = false, kBf16 = false, kStacked = true;
+  static constexpr int kPieces = 2, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 2;
+  static constexpr bool kTf32 = false, kBf16 = false;
+  __device__ static constexpr int corr_x(int j) { return j; }
+  __device__ static constexpr int corr_m(int j) { return 1 - j; }
 };
 struct SplitBf16x6 {
   static constexpr int kPieces = 3, kImgPieces = 3, kOut = 64, kDBufs = 2, kCorr = 5;
-  static constexpr bool kTf32 = false, kBf16 = true, kStacked = false;
+  static constexpr bool kTf32 = false, kBf16 = true;
   // (0,2) (1,1) (2,0) (0,1) (1,0): second-order terms before first-order
   __device__ static constexpr int corr_x(int j) { return j < 3 ? j : j - 3; }
   __device__ static constexpr int corr_m(int j) { return j < 3 ? 2 - j : 4 - j; }
 };
 struct SplitTf32x3 {
   static constexpr int kPieces = 2, kImgPieces = 2, kOut = 64, kDBufs = 2, kCorr = 2;
-  static constexpr bool kTf32 = true, kBf16 = false, kStacked = false;
+  static constexpr bool kTf32 = true, kBf16 = false;
   __device__ static constexpr int corr_x(int j) { return j; }
   __device__ static constexpr int corr_m(int j) { return 1 - j; }
 };
 struct SplitBf16x3 {     // the first two BF16X6 pieces of M
-  static constexpr int kPieces = 2, kImgPieces = 3, kOut = 128, kDBufs = 1;
-  static constexpr bool kTf32 = false, kBf16 = true, kStacked = true;
+  static constexpr int kPieces = 2, kImgPieces = 3, kOut = 128, kDBufs = 1, kCorr = 2;
+  static constexpr bool kTf32 = false, kBf16 = true;
+  __device__ static constexpr int corr_x(int j) { return j; }
+  __device__ static constexpr int corr_m(int j) { return 1 - j; }
 };
 struct SplitTf32x1 {
   static constexpr int kPieces = 1, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 0;
-  static constexpr bool kTf32 = true, kBf16 = false, kStacked = false;
+  static constexpr bool kTf32 = true, kBf16 = false;
   __device__ static constexpr int corr_x(int) { return 0; }
   __device__ static constexpr int corr_m(int) { return 0; }
 };
@@ -120,11 +112,7 @@ struct Layout {
   static constexpr int kBlocksK = kN2 / kRowElems;          // 128-byte K blocks of B
   static constexpr int kPieceCols = kChunkK * kElem / 4;    // TMEM columns per A piece per chunk
   static constexpr int kABufCols = S::kPieces * kPieceCols;
-  // stacked: accumulators in columns [0, 3 kOut), the A ring in the rest
-  static constexpr uint32_t kDCols = S::kStacked ? 3 * S::kOut : kTmemCols - kRingCols;
-  static constexpr uint32_t kRing0 = S::kStacked ? kDCols : 0;
-  static constexpr uint32_t kDCol0 = S::kStacked ? 0 : kRingCols;
-  static constexpr int kABufs = (kTmemCols - kDCols) / kABufCols;
+  static constexpr int kABufs = kRingCols / kABufCols;
   static constexpr int kKStep = S::kTf32 ? 8 : 16;          // K per MMA
   static constexpr int kParts = kN2 / S::kOut;
   static constexpr int kBBlock = S::kOut * 128;             // one (piece, K block) of B
@@ -139,11 +127,8 @@ struct Layout {
   static constexpr int kOffMisc = kOffBar + kNumBars * 8;
   static constexpr int kSmem = kOffMisc + 16 + 1024;
   static_assert(kSmem <= 232448, "shared memory");
-  static_assert(S::kStacked || kABufs >= kChunks / kGroups, "a K half's chunks must fit the A ring");
-  static_assert(S::kStacked || S::kDBufs * kGroups * S::kOut == (int)(kTmemCols - kRingCols),
-                "TMEM split");
-  static_assert(!S::kStacked || (S::kPieces == 2 && S::kDBufs == 1 && S::kOut == 128 && kABufs >= 2),
-                "stacked layout");
+  static_assert(kABufs >= kChunks / kGroups, "a K half's chunks must fit the A ring");
+  static_assert(S::kDBufs * kGroups * S::kOut == (int)(kTmemCols - kRingCols), "TMEM split");
   static_assert(kDcRing >= S::kDBufs + 2, "DC ring depth");
   static_assert(!(S::kTf32 && S::kBf16), "one piece type");
 };
@@ -267,10 +252,7 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
   // holds kImgPieces * 256 rows: piece p's output t at row p * 256 + t)
   for (int i = tid; i < L::kBBytes / 16; i += kThreads) {
     const int blk = i / (L::kBBlock / 16), off = i % (L::kBBlock / 16);
-    // stacked: K-block-major, so a K block's pieces (hi rows, then lo rows)
-    // are adjacent and one MMA of N = 2 kOut reads both
-    const int piece = S::kStacked ? blk % S::kPieces : blk / L::kBlocksK;
-    const int kb = S::kStacked ? blk / S::kPieces : blk % L::kBlocksK;
+    const int piece = blk / L::kBlocksK, kb = blk % L::kBlocksK;
     const size_t src_row0 = (size_t)kb * S::kImgPieces * kN2 + piece * kN2 + part * kOut;
     reinterpret_cast<uint4 *>(s_b)[i] = __ldg(pieces + src_row0 * 8 + off);
   }
@@ -306,37 +288,6 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
     // products, then of the main product; a chunk's A buffer is released
     // after its main product.
     int q = 0, last_q = -1;
-    if constexpr (S::kStacked) {
-      // per chunk and K step: D[0, 2 kOut) (+)= x_hi [M_hi | M_lo]^T and
-      // D[2 kOut, 3 kOut) (+)= x_lo M_hi^T; the chunk's A buffer is released
-      // after its four MMAs
-      for (int it = 0; it < my_tiles; ++it) {
-        if (!wait_bounded(&d_empty[0], (it & 1) ^ 1, s_abort, err, kRoleMma | (it << 8)))
-          goto mma_done_label;
-        const uint32_t t_d = tmem + L::kDCol0;
-        for (int kc = 0; kc < kChunks; ++kc) {
-          const int qc = q + kc, a = qc % kABufs;
-          if (!wait_bounded(&a_full[a], (qc / kABufs) & 1, s_abort, err, kRoleMma | (qc << 8)))
-            goto mma_done_label;
-          tc_fence_after();
-          const uint32_t t_a = tmem + L::kRing0 + a * L::kABufCols;
-          const int kb = kc * kChunkK / L::kRowElems;
-          const int kofs = (kc * kChunkK % L::kRowElems) * L::kElem / 16;   // 16-byte units
-          const uint64_t b = desc_sw128(smem_u32(s_b + kb * S::kPieces * L::kBBlock)) + kofs;
-#pragma unroll
-          for (int kk = 0; kk < kChunkK / L::kKStep; ++kk) {
-            const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-            mma_f16_ts(t_d, t_a + 8 * kk, b + 2 * kk, idesc_f16(128, 2 * kOut, S::kBf16), acc);
-            mma_f16_ts(t_d + 2 * kOut, t_a + L::kPieceCols + 8 * kk, b + 2 * kk,
-                       idesc_f16(128, kOut, S::kBf16), acc);
-          }
-          tc_commit(&a_done[a]);
-          last_q = qc;
-        }
-        q += kChunks;
-        tc_commit(&d_full[0]);
-      }
-    } else
     for (int it = 0; it < my_tiles; ++it) {
       const int db = it % kDBufs;
       if (!wait_bounded(&d_empty[db], ((it / kDBufs) & 1) ^ 1, s_abort, err, kRoleMma | (it << 8)))
@@ -415,7 +366,7 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
                                kRoleConv | (q << 8)))
           goto conv_done;
         tc_fence_after();
-        convert_store<S>(v, tmem + lane_base + L::kRing0 + a * L::kABufCols);
+        convert_store<S>(v, tmem + lane_base + a * L::kABufCols);
         tmem_st_wait();
         tc_fence_before();
         mbar_arrive(&a_full[a]);
@@ -438,32 +389,18 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
       if (!warp_wait_bounded(&dc_full[r], (it / kDcRing) & 1, s_abort, err, kRoleEpi | (it << 8)))
         break;
       const float x0 = s_dc[r * kTile + row];
-      const uint32_t t_d = tmem + lane_base + L::kDCol0 + db * kGroups * kOut;
-      // read this warp's slices of the accumulators and add them (the two K
-      // halves; stacked: main + (x_hi M_lo + x_lo M_hi)), then release D
-      // before staging and storing, so the next tile's MMAs need not wait
-      // for the stores (16x16 F16X3: 135 -> 128 us at 8192^2)
+      const uint32_t t_d = tmem + lane_base + kRingCols + db * kGroups * kOut;
+      // read this warp's slices of both K-half accumulators and add them,
+      // then release D before staging and storing, so the next tile's MMAs
+      // need not wait for the stores (16x16 F16X3: 135 -> 128 us at 8192^2)
       float acc[kJ][32];
 #pragma unroll
       for (int jj = 0; jj < kJ; ++jj) {
         const int j = hc * kJ + jj;
-        if constexpr (S::kStacked) {
+        uint32_t d0[32], d1[32];
+        tmem_ld32x2(t_d + 32 * j, t_d + kOut + 32 * j, d0, d1);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint32_t dm[16], c1[16], c2[16];
-            const uint32_t tc = t_d + 32 * j + 16 * h;
-            tmem_ld16x3(tc, tc + kOut, tc + 2 * kOut, dm, c1, c2);
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-              acc[jj][16 * h + c] = __uint_as_float(dm[c]) +
-                                    (__uint_as_float(c1[c]) + __uint_as_float(c2[c]));
-          }
-        } else {
-          uint32_t d0[32], d1[32];
-          tmem_ld32x2(t_d + 32 * j, t_d + kOut + 32 * j, d0, d1);
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[jj][c] = __uint_as_float(d0[c]) + __uint_as_float(d1[c]);
-        }
+        for (int c = 0; c < 32; ++c) acc[jj][c] = __uint_as_float(d0[c]) + __uint_as_float(d1[c]);
       }
       tc_fence_before();
       mbar_arrive(&d_empty[db]);               // this warp's columns of D have been read
