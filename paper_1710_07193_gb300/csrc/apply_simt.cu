@@ -245,17 +245,21 @@ apply_simt_db_kernel(const float *__restrict__ M32, const float *__restrict__ Md
 }
 
 // 16x16 blocks, FP32 input: M (256 KB) does not fit shared memory, so it
-// streams in 128 x 32 chunks, 16 per 32-block tile (two passes of 128
+// streams in 128 x 32 chunks, 16 per 64-block tile (two passes of 128
 // outputs, eight 32-input chunks each).  The chunk sequence is the same for
 // every tile, so the next chunk is always known: it is copied with cp.async
-// into the second of two chunk buffers while the current one computes.  Each
-// output still sums its inputs in order k = 0..255 with one FMA chain (the
-// DC term last), so the bits equal apply_simt_kernel's.  Outputs go straight
-// from registers to global memory (for each of a thread's outputs, the 16
-// threads of its block row store 64 contiguous bytes), so no staging buffer:
-// 70 KB of shared memory a CTA, three CTAs per SM.
+// into the second of two chunk buffers while the current one computes, and
+// one barrier a chunk both publishes its copies and retires the previous
+// chunk's readers.  Each thread holds an 8 x 8 register tile (8 blocks x 8
+// outputs: 16 shared-memory loads per 256 FMAs); each output still sums its
+// inputs in order k = 0..255 with one FMA chain (the DC term last), so the
+// bits equal apply_simt_kernel's.  Outputs go straight from registers to
+// global memory (for each of a thread's outputs, the 16 threads of its block
+// row store 64 contiguous bytes), so no staging buffer: 101 KB of shared
+// memory a CTA, two CTAs per SM (a 4 x 8 register tile with three CTAs per
+// SM measured 8% slower).
 struct Simt16Db {
-  static constexpr int N2 = 256, TB = 32, TN = 128, TK = 32, RB = 4, RN = 8;
+  static constexpr int N2 = 256, TB = 64, TN = 128, TK = 32, RB = 8, RN = 8;
   static constexpr int TPB = TB / RB, TPN = TN / RN;     // 8 x 16 = 128 threads
   static constexpr int kXP = N2 + 4, kMP = TK + 4;
   static constexpr int kChunks = (N2 / TN) * (N2 / TK);  // 16 per tile
@@ -264,7 +268,7 @@ struct Simt16Db {
   static_assert(TPB * TPN == 128, "128 threads");
 };
 
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, 2)
 apply_simt16_db_kernel(const float *__restrict__ M32, const float *__restrict__ Mdc,
                        const float *__restrict__ x, int64_t nblocks, float *y) {
   using C = Simt16Db;
@@ -306,10 +310,9 @@ apply_simt16_db_kernel(const float *__restrict__ M32, const float *__restrict__ 
 #pragma unroll
         for (int j = 0; j < C::RN; ++j) acc[i][j] = 0.f;
       for (int k0 = 0; k0 < C::N2; k0 += C::TK, ++cnt) {
-        __syncthreads();   // every thread is done with the buffer of chunk cnt - 1
+        cp_async_wait_group<0>();   // this thread's copies of chunk cnt (the only ones in flight)
+        __syncthreads();            // every thread's have landed, and chunk cnt - 1 is read
         issue_m((cnt + 1) % C::kChunks, (cnt + 1) & 1);
-        cp_async_wait_group<1>();   // this thread's copies of chunk cnt have landed
-        __syncthreads();            // and every other thread's
         const float *Ms = Mb + (cnt & 1) * C::kMFloats;
 #pragma unroll 2
         for (int k4 = 0; k4 < C::TK; k4 += 4) {

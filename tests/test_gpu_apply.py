@@ -92,7 +92,7 @@ def test_simt_tile_configs_agree(dctf, ragged_source):
     op.release()
 
 
-@pytest.mark.parametrize("nb", [1, 31, 33, 1000, 40000])
+@pytest.mark.parametrize("nb", [1, 31, 33, 63, 65, 1000, 40000])
 def test_simt16_double_buffered_same_bits(dctf, n16_source, nb):
     """16x16 FP32 CUDA cores: the kernel that streams M's chunks double-
     buffered (FP32 input) gives the same bits as the single-buffered kernel
