@@ -242,10 +242,15 @@ __device__ __forceinline__ uint32_t pixel_u8_low_byte(float p) {
 // run on the same SMs while this kernel streams.
 enum : int { kModeBlocks = 0, kModePixels = 1, kModePlanar = 2, kModeHost = 3 };
 
-// The pixel mode runs eight epilogue warps (two per TMEM lane quarter, each
-// taking half of a block's pixel rows): its per-tile epilogue (64 roundings
-// and packings a block) bounds it.  Its 512 threads get 128 registers each.
+// The pixel mode runs eight epilogue warps in two sets of four (one warp per
+// TMEM lane quarter), the sets taking alternate tiles, so two tiles' 64
+// roundings and packings a block are in flight at once: its per-tile
+// epilogue is a latency chain (TMEM load, DC value, rounding, stores) that
+// bounds it otherwise.  Its 512 threads get 128 registers each.
 __host__ __device__ constexpr int epi_warps(int mode) { return mode == kModePixels ? 8 : 4; }
+// threads that release an accumulator buffer (four warps, one per lane
+// quarter, in every mode)
+constexpr int kEpiReleaseThreads = 128;
 __host__ __device__ constexpr int block_threads(int mode) { return 256 + 32 * epi_warps(mode); }
 
 template <typename IoT, int S, int NS, bool kGroup, int kMode>
@@ -284,7 +289,7 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
     }
     for (int b = 0; b < kBufs; ++b) {
       mbar_init(&a_full[b], 128); mbar_init(&mma_done[b], 1);
-      mbar_init(&d_empty[b], 32 * epi_warps(kMode));
+      mbar_init(&d_empty[b], kEpiReleaseThreads);
     }
     for (int r = 0; r < kDcRing; ++r) mbar_init(&dc_full[r], 128);
     for (int k = 0; k < NS; ++k) {   // released by the converter, the epilogue and the MMA
@@ -532,19 +537,19 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       if (t.seg_first &&
           !warp_wait_bounded(&slot_full[k], (t.seg / NS) & 1, s_abort, err, kRoleEpi | (it << 8)))
         break;
-      if (!warp_wait_bounded(&mma_done[b], pb, s_abort, err, kRoleEpi | (it << 8))) break;
-      tc_fence_after();
       if constexpr (kMode == kModePixels) {
-        // warp 8 + 4 hc + wr: TMEM lanes 32 wr.. (its blocks), output columns
-        // 32 hc .. 32 hc + 31, i.e. pixel rows 4 hc .. 4 hc + 3 of each block
-        const int hc = (warp - 8) >> 2;
-        float px[32];
-        {
-          uint32_t d[32];
-          tmem_ld32(tmem + lane_base + b * 128 + 64 + 32 * hc, d);
-#pragma unroll
-          for (int c = 0; c < 32; ++c) px[c] = __uint_as_float(d[c]);
+        // warp 8 + 4 set + wr: TMEM lanes 32 wr.. (its blocks), every output
+        // column, tiles it with it % 2 == set (TMEM buffers b of that parity)
+        const int set = (warp - 8) >> 2;
+        if ((it & 1) != set) {
+          if (t.seg_last) mbar_arrive(&slot_empty[k]);   // the other set's tile
+          ++it;
+          continue;
         }
+        if (!warp_wait_bounded(&mma_done[b], pb, s_abort, err, kRoleEpi | (it << 8))) break;
+        tc_fence_after();
+        uint32_t d[2][32];
+        tmem_ld32x2(tmem + lane_base + b * 128 + 64, tmem + lane_base + b * 128 + 96, d[0], d[1]);
         // the DC value is read before D[b] is released (see below)
         if (!warp_wait_bounded(&dc_full[r], pr, s_abort, err, kRoleEpi | (it << 8))) break;
         const float x0 = s_dc[r * kTile + row];
@@ -552,43 +557,50 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
         mbar_arrive(&d_empty[b]);
         const GroupItem &gi = items[t.item];
         const float out_scale = gi.out_scale;
-        const float4 *mdc4 =
-            reinterpret_cast<const float4 *>(s_slot + k * kSlotBytes + kSlotPieces) + 8 * hc;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 md = mdc4[u];
-          px[4 * u] = fmaf(px[4 * u], out_scale, md.x * x0);
-          px[4 * u + 1] = fmaf(px[4 * u + 1], out_scale, md.y * x0);
-          px[4 * u + 2] = fmaf(px[4 * u + 2], out_scale, md.z * x0);
-          px[4 * u + 3] = fmaf(px[4 * u + 3], out_scale, md.w * x0);
-        }
         // block bk of the item covers image rows 8 (bk / bw) + 0..7 and
         // columns 8 (bk % bw) + 0..7; its pixel (i, j) is output i * 8 + j.
         // The lanes of a warp hold consecutive blocks, so each row's 8-byte
         // stores of a warp are contiguous.
         // 32-bit block coordinates: an item has fewer than 2^31 blocks
         const int bk = t.row0 + row, bw = (int)gi.bw;
-        if (row < t.rows && bk < gi.nblocks) {
-          const int by = bk / bw, bx = bk - by * bw;
-          uint8_t *dst = gi.img + ((int64_t)by * 8 + 4 * hc) * gi.pitch + (int64_t)bx * 8;
+        const bool live = row < t.rows && bk < gi.nblocks;
+        const int by = bk / bw, bx = bk - by * bw;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            uint32_t w[2];
+        for (int hc = 0; hc < 2; ++hc) {   // pixel rows 4 hc .. 4 hc + 3
+          const float4 *mdc4 =
+              reinterpret_cast<const float4 *>(s_slot + k * kSlotBytes + kSlotPieces) + 8 * hc;
+          float px[32];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float *a = px + 8 * i + 4 * h;
-              // bytes b0..b3 into one word (PRMT: low bytes of four words)
-              w[h] = __byte_perm(
-                  __byte_perm(pixel_u8_low_byte(a[0]), pixel_u8_low_byte(a[1]), 0x0040),
-                  __byte_perm(pixel_u8_low_byte(a[2]), pixel_u8_low_byte(a[3]), 0x0040), 0x5410);
+          for (int u = 0; u < 8; ++u) {
+            const float4 md = mdc4[u];
+            px[4 * u] = fmaf(__uint_as_float(d[hc][4 * u]), out_scale, md.x * x0);
+            px[4 * u + 1] = fmaf(__uint_as_float(d[hc][4 * u + 1]), out_scale, md.y * x0);
+            px[4 * u + 2] = fmaf(__uint_as_float(d[hc][4 * u + 2]), out_scale, md.z * x0);
+            px[4 * u + 3] = fmaf(__uint_as_float(d[hc][4 * u + 3]), out_scale, md.w * x0);
+          }
+          if (live) {
+            uint8_t *dst = gi.img + ((int64_t)by * 8 + 4 * hc) * gi.pitch + (int64_t)bx * 8;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              uint32_t w[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const float *a = px + 8 * i + 4 * h;
+                // bytes b0..b3 into one word (PRMT: low bytes of four words)
+                w[h] = __byte_perm(
+                    __byte_perm(pixel_u8_low_byte(a[0]), pixel_u8_low_byte(a[1]), 0x0040),
+                    __byte_perm(pixel_u8_low_byte(a[2]), pixel_u8_low_byte(a[3]), 0x0040), 0x5410);
+              }
+              *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
             }
-            *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
           }
         }
         if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's G[:,0]
         ++it;
         continue;
       }
+      if (!warp_wait_bounded(&mma_done[b], pb, s_abort, err, kRoleEpi | (it << 8))) break;
+      tc_fence_after();
       float acc[64];
       {
         uint32_t d0[32], d1[32];
