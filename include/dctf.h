@@ -301,9 +301,9 @@ dctf_status dctf_group_create(const dctf_group_item *items, int nitems,
 dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream);
 
 /* Autotuner: time each candidate (CTA count x tile height x shared-memory
- * layout, i.e. input stages x operator slots) `reps` times on this group (it
- * really runs the group: no item may be in place; EINVAL otherwise), keep
- * the fastest for this group and cache it for its (device, kind, size
+ * layout, i.e. input stages x operator slots) in `reps` rounds of four
+ * back-to-back launches on this group (it really runs the group: no item
+ * may be in place; EINVAL otherwise), keep the fastest median for this group and cache it for its (device, kind, size
  * class).  If the environment variable DCTF_TUNE_CACHE names a file, the
  * cache is loaded from it when the first group is created and written back
  * after each tuning.  Synchronises `stream`. */

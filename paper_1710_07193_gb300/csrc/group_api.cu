@@ -13,9 +13,10 @@
 // balance small items better) and the shared-memory layout (input stages x
 // operator slots: more stages keep more loads in flight, two slots let
 // operator switches overlap the previous item's tiles).  dctf_group_tune
-// times every candidate on the group itself (CUDA events, median of `reps`)
-// and keeps the fastest; the choice is also cached per (device, I/O type,
-// size class) and used as the default for later groups of that class.  With
+// times every candidate on the group itself (CUDA events around four
+// back-to-back launches, median of `reps` rounds) and keeps the fastest; the
+// choice is also cached per (device, I/O type, size class) and used as the
+// default for later groups of that class.  With
 // DCTF_TUNE_CACHE naming a file, the cache is read from it at the first
 // group and written back after every tuning, so later processes start from
 // the tuned choice.
@@ -309,6 +310,7 @@ dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps) {
   if (reps < 1) reps = 5;
   const int sms = sm_count(g->device);
   static const int kFrac[][2] = {{1, 1}, {3, 4}, {1, 2}};
+  constexpr int kBackToBack = 4;
   cudaEvent_t e0, e1;
   DCTF_CUDA(cudaEventCreate(&e0));
   DCTF_CUDA(cudaEventCreate(&e1));
@@ -320,8 +322,12 @@ dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps) {
       const int grid = std::max(1, sms * f[0] / f[1]);
       std::vector<float> ts;
       for (int r = 0; r < reps + 1; ++r) {
+        // kBackToBack launches between the events, as a graph replays them:
+        // one launch alone would add its launch latency and its fill and
+        // drain to every candidate alike
         cudaEventRecord(e0, stream);
-        cudaError_t e = launch(g, grid, take, v, stream);
+        cudaError_t e = cudaSuccess;
+        for (int q = 0; q < kBackToBack && e == cudaSuccess; ++q) e = launch(g, grid, take, v, stream);
         cudaEventRecord(e1, stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
@@ -331,7 +337,7 @@ dctf_status dctf_group_tune(dctf_group *g, dctf_stream_t stream, int reps) {
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) ts.push_back(ms);   // first run warms the caches
+        if (r > 0) ts.push_back(ms / kBackToBack);   // first round warms the caches
       }
       std::sort(ts.begin(), ts.end());
       const float med = ts[ts.size() / 2];
