@@ -109,7 +109,7 @@ template <class S>
 struct Layout {
   // Input chunks arrive ~2,100 cycles after their TMA load is issued, and a
   // stage is issued again only once the converter has read it, so the
-  // chunk rate is stages / (load latency + conversion): the CTA-pair splits
+  // chunk rate is stages / (load latency + conversion): the two-CTA splits
   // (M's 128 output rows resident, 128 KB) fit a fourth stage because each
   // epilogue warp stages its output in 16-column halves (16x16 F16X3:
   // 117 -> ~111 us at 8192^2); the four-CTA splits keep three.

@@ -298,12 +298,13 @@ def n16_source():
     return blocks, x.astype(np.float32)
 
 
-@pytest.mark.parametrize("nb", [1, 127, 129, 1000, 40000])
+@pytest.mark.parametrize("nb", [1, 127, 129, 255, 257, 1000, 40000])
 @pytest.mark.parametrize("prec", ["F16X3", "BF16X6", "TF32X3"])
 def test_n16_tensor_core_ragged(dctf, n16_source, nb, prec):
     """16x16 blocks, perturbed 9x9 Gaussian, border replication: the
     tensor-core kernels (outputs split over 2 or 4 CTAs, K-chunked input)
-    on block counts that leave partial tiles and idle CTA groups."""
+    on block counts that leave partial tiles (one block, a tile minus or
+    plus one, two tiles minus or plus one) and idle CTA groups."""
     blocks, x = n16_source
     x, blocks = x[:nb], blocks[:nb]
     w, a = datagen.large_mask(), (4, 4)
