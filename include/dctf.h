@@ -442,6 +442,13 @@ dctf_status dctf_server_wait(dctf_server *s, uint64_t ticket, int timeout_ms);
 
 dctf_status dctf_server_stats(dctf_server *s, dctf_stats *out);
 
+/* Start a new statistics window: clears the latencies and every counter of
+ * dctf_stats (hbm_peak restarts at the bytes in use); the operator cache,
+ * queued and running requests are untouched (requests still running when
+ * it is called count in the new window, with their original submit time).
+ * For measuring a steady state after a warm-up. */
+dctf_status dctf_server_reset_stats(dctf_server *s);
+
 /* Finish every queued and running request, then free everything. */
 void dctf_server_destroy(dctf_server *s);
 

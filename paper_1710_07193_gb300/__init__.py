@@ -379,6 +379,7 @@ _SIGS.update({
     "dctf_server_submit": (_i32, [_vp, _vp, _vp]),
     "dctf_server_wait": (_i32, [_vp, ctypes.c_uint64, _i32]),
     "dctf_server_stats": (_i32, [_vp, _vp]),
+    "dctf_server_reset_stats": (_i32, [_vp]),
     "dctf_server_destroy": (None, [_vp]),
 })
 
@@ -448,6 +449,10 @@ class Server:
         s = _Stats()
         _check(load().dctf_server_stats(self.handle, ctypes.addressof(s)))
         return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def reset_stats(self) -> None:
+        """Start a new statistics window (the operator cache stays warm)."""
+        _check(load().dctf_server_reset_stats(self.handle))
 
     def close(self) -> None:
         if self.handle:

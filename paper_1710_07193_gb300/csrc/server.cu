@@ -640,6 +640,18 @@ dctf_status dctf_server_stats(dctf_server *s, dctf_stats *out) {
   return DCTF_OK;
 }
 
+dctf_status dctf_server_reset_stats(dctf_server *s) {
+  if (s == nullptr) return set_error(DCTF_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat_ms.clear();
+  s->completed = s->failed = s->batches = s->blocks = s->hits = s->misses = 0;
+  s->direct = s->budget_waits = 0;
+  s->hbm_peak = s->arena.used();
+  s->t_first_submit = s->t_last_done = 0;
+  s->max_batch_seen = 0;
+  return DCTF_OK;
+}
+
 void dctf_server_destroy(dctf_server *s) {
   if (s == nullptr) return;
   {

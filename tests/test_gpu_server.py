@@ -259,3 +259,28 @@ def test_admission_waits_for_budget(dctf):
     assert st["budget_waits"] >= 1
     assert 0 < st["hbm_peak"] <= budget and st["hbm_in_use"] == 0
     srv.close()
+
+
+def test_reset_stats_starts_a_new_window(dctf):
+    """dctf_server_reset_stats clears the latencies and counters but keeps
+    the operator cache: the same mask after a reset is a cache hit, and the
+    new window counts only the requests that complete in it."""
+    srv = dctf.Server(hbm_budget_bytes=64 << 20, max_inflight=2, max_batch_requests=4)
+    w, a, bnd = datagen.serving_mask(5)
+    img = datagen.synthetic_image(256, 256, datagen.rng(97, 9, 0))
+    x, q = quantised(img, 1)
+    outs = [np.zeros_like(x) for _ in range(3)]
+    srv.wait(srv.submit([x], [outs[0]], [q], w, a, bnd))
+    st = srv.stats()
+    assert st["completed"] == 1 and st["cache_misses"] == 1
+    srv.reset_stats()
+    st = srv.stats()
+    assert st["completed"] == 0 and st["cache_misses"] == 0 and st["cache_hits"] == 0
+    assert st["p99_ms"] == 0 and st["batches"] == 0 and st["budget_waits"] == 0
+    for o in outs[1:]:
+        srv.wait(srv.submit([x], [o], [q], w, a, bnd))
+    st = srv.stats()
+    assert st["completed"] == 2 and st["cache_misses"] == 0 and st["cache_hits"] == 2
+    assert st["p50_ms"] > 0 and st["failed"] == 0
+    assert np.array_equal(outs[1], outs[0]) and np.array_equal(outs[2], outs[0])
+    srv.close()
