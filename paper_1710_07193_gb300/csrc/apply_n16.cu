@@ -130,7 +130,7 @@ struct Layout {
   static constexpr int kOffMdc = kOffOut + 2 * 4 * kOutSlab;
   static constexpr int kOffDc = kOffMdc + S::kOut * 4;
   static constexpr int kOffBar = kOffDc + kDcRing * kTile * 4;
-  static constexpr int kNumBars = 2 * kStages + 2 * kABufs + 2 * S::kDBufs + kDcRing;
+  static constexpr int kNumBars = 2 * kStages + 2 * kABufs + 2 * S::kDBufs + kDcRing + 1;
   static constexpr int kOffMisc = kOffBar + kNumBars * 8;
   static constexpr int kSmem = kOffMisc + 16 + 1024;
   static_assert(kSmem <= 232448, "shared memory");
@@ -237,6 +237,7 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
   uint64_t *d_full = a_done + kABufs;           // [kDBufs]
   uint64_t *d_empty = d_full + kDBufs;          // [kDBufs]
   uint64_t *dc_full = d_empty + kDBufs;         // [kDcRing]
+  uint64_t *b_full = dc_full + kDcRing;         // the resident pieces have landed
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(base + L::kOffMisc);
   volatile int *s_abort = reinterpret_cast<volatile int *>(base + L::kOffMisc + 4);
 
@@ -250,18 +251,10 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
     for (int a = 0; a < kABufs; ++a) { mbar_init(&a_full[a], 128); mbar_init(&a_done[a], 1); }
     for (int d = 0; d < kDBufs; ++d) { mbar_init(&d_full[d], 1); mbar_init(&d_empty[d], 256); }
     for (int r = 0; r < kDcRing; ++r) mbar_init(&dc_full[r], 128);
+    mbar_init(b_full, 1);
     *s_abort = 0;
     mbar_fence_init();
     tma_prefetch_map(&tm_in);
-  }
-  // resident B: for each piece and 128-byte K block, this part's kOut rows
-  // (a contiguous block of the operator's piece image, whose K block kb
-  // holds kImgPieces * 256 rows: piece p's output t at row p * 256 + t)
-  for (int i = tid; i < L::kBBytes / 16; i += kThreads) {
-    const int blk = i / (L::kBBlock / 16), off = i % (L::kBBlock / 16);
-    const int piece = blk / L::kBlocksK, kb = blk % L::kBlocksK;
-    const size_t src_row0 = (size_t)kb * S::kImgPieces * kN2 + piece * kN2 + part * kOut;
-    reinterpret_cast<uint4 *>(s_b)[i] = __ldg(pieces + src_row0 * 8 + off);
   }
   if (tid < kOut) s_mdc[tid] = __ldg(Mdc + part * kOut + tid);
   fence_async_smem();
@@ -273,6 +266,18 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
+    // resident B first: for each piece and 128-byte K block, this part's
+    // kOut rows, a contiguous 16 KB (kOut = 128) or 8 KB block of the
+    // operator's piece image (K block kb holds kImgPieces * 256 rows: piece
+    // p's output t at row p * 256 + t), copied in the background while the
+    // first input chunks load and convert; the MMA warp waits for it.  (A
+    // thread-by-thread copy before the roles start cost ~7 us a launch.)
+    mbar_arrive_expect_tx(b_full, L::kBBytes);
+    for (int blk = 0; blk < S::kPieces * L::kBlocksK; ++blk) {
+      const int piece = blk / L::kBlocksK, kb = blk % L::kBlocksK;
+      const size_t src_row0 = (size_t)kb * S::kImgPieces * kN2 + piece * kN2 + part * kOut;
+      bulk_load(s_b + blk * L::kBBlock, pieces + src_row0 * 8, L::kBBlock, b_full);
+    }
     int q = 0, issued = 0;
     for (int it = 0; it < my_tiles; ++it) {
       const int tile = grp + it * ngroups;
@@ -287,6 +292,7 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
       }
     }
   producer_done:
+    wait_drain(b_full, 0, err, kRoleDrain);
     for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
       wait_drain(&full_in[k % kStages], (k / kStages) & 1, err, kRoleDrain);
   } else if (warp == 1 && lane == 0) {
@@ -295,6 +301,8 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
     // products, then of the main product; a chunk's A buffer is released
     // after its main product.
     int q = 0, last_q = -1;
+    if (my_tiles > 0 && !wait_bounded(b_full, 0, s_abort, err, kRoleMma))
+      goto mma_done_label;
     for (int it = 0; it < my_tiles; ++it) {
       const int db = it % kDBufs;
       if (!wait_bounded(&d_empty[db], ((it / kDBufs) & 1) ^ 1, s_abort, err, kRoleMma | (it << 8)))
