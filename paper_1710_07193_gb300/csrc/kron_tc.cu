@@ -83,7 +83,7 @@ constexpr int kOffT = kOffB2 + kKronPieceBytes / 2;
 constexpr int kOffMdc = kOffT + 2 * 4 * 2 * kTBlk * 4;   // two transposer sets
 constexpr int kOffDc = kOffMdc + kN2 * 4;
 constexpr int kOffBar = kOffDc + kDcRing * kUnit * 4;
-constexpr int kNumBars = 2 * kStages + 2 * kA1Bufs + 6 * 2 + 2 * kDcRing;
+constexpr int kNumBars = 2 * kStages + 2 * kA1Bufs + 6 * 2 + 2 * kDcRing + 1;
 constexpr int kOffMisc = kOffBar + kNumBars * 8;
 constexpr int kSmem = kOffMisc + 16 + 1024;
 static_assert(kSmem <= 232448, "shared memory");
@@ -132,6 +132,7 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
   uint64_t *d2_empty = d2_full + 2;           // [2] epilogue -> MMA
   uint64_t *dc_full = d2_empty + 2;           // [kDcRing] converter -> epilogue
   uint64_t *dc_empty = dc_full + kDcRing;     // [kDcRing] epilogue -> converter
+  uint64_t *b_full = dc_empty + kDcRing;      // the pieces images have landed
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(base + kOffMisc);
   volatile int *s_abort = reinterpret_cast<volatile int *>(base + kOffMisc + 4);
 
@@ -153,14 +154,12 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
       mbar_init(&d2_full[b], 1);   mbar_init(&d2_empty[b], 128);
     }
     for (int r = 0; r < kDcRing; ++r) { mbar_init(&dc_full[r], 128); mbar_init(&dc_empty[r], 128); }
+    mbar_init(b_full, 1);
     *s_abort = 0;
     mbar_fence_init();
     tma_prefetch_map(&tm_in);
   }
-  // both pieces images (32 KB, already in the swizzled B layout) and M[:, 0]
-  for (int i = tid; i < kKronPieceBytes / 16; i += kThreads)
-    reinterpret_cast<uint4 *>(s_b1)[i] = __ldg(pieces + i);
-  if (tid < kN2) s_mdc[tid] = __ldg(Mdc + tid);
+  if (tid < kN2) s_mdc[tid] = __ldg(Mdc + tid);   // M[:, 0]
   fence_async_smem();
   if (warp == 2) { tmem_alloc(s_tmem, kTmemCols); tmem_relinquish(); }
   tc_fence_before();
@@ -170,6 +169,12 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
+    // both pieces images first (32 KB, already in the swizzled B layout), in
+    // the background of the first input loads; the issuers wait for them
+    mbar_arrive_expect_tx(b_full, kKronPieceBytes);
+    for (int h = 0; h < 2; ++h)
+      bulk_load(s_b1 + h * (kKronPieceBytes / 2), pieces + h * (kKronPieceBytes / 32),
+                kKronPieceBytes / 2, b_full);
     int issued = 0;
     for (int k = 0; k < my_units; ++k) {
       const int s = k % kStages;
@@ -183,12 +188,14 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
     }
     for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
       wait_drain(&full_in[k % kStages], (k / kStages) & 1, err, kRoleDrain);
+    wait_drain(b_full, 0, err, kRoleDrain);
   } else if (warp == 1 && lane == 0 && terms) {
     // ---------------------------------------------------------- pass-1 issuer
     // D1 = x_hi B_lo^T + x_lo B_hi^T + x_hi B_hi^T for every step, in order
     uint64_t *last_bar = nullptr;
     uint32_t last_ph = 0;
-    for (int st = 0; st < nsteps; ++st) {
+    const bool b_ok = nsteps == 0 || wait_bounded(b_full, 0, s_abort, err, kRoleMma);
+    for (int st = 0; b_ok && st < nsteps; ++st) {
       const int k = st / NG, g = st % NG, ng = min(4, rank - 4 * g);
       const int ab = k % kA1Bufs, db = st & 1;
       if (g == 0 && !wait_bounded(&a1_full[ab], (k / kA1Bufs) & 1, s_abort, err,
@@ -215,7 +222,8 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
     // per term, D2[0:32] (+)= Z_hi [A_hi | A_lo]^T, D2[32:48] (+)= Z_lo A_hi^T
     uint64_t *last_bar = nullptr;
     uint32_t last_ph = 0;
-    for (int st = 0; st < nsteps; ++st) {
+    const bool b_ok = nsteps == 0 || wait_bounded(b_full, 0, s_abort, err, kRoleMma);
+    for (int st = 0; b_ok && st < nsteps; ++st) {
       const int k = st / NG, g = st % NG, ng = min(4, rank - 4 * g);
       const int a2b = st & 1, d2b = k & 1;
       if (!wait_bounded(&a2_full[a2b], (st >> 1) & 1, s_abort, err, kRoleMma | (st << 8)))
