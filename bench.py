@@ -46,7 +46,7 @@ GRAPH_STEPS = 200       # steps per captured graph; the timed loop replays sever
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "7105c3db73e5b065cc12bee4183b2c81b1a971ea": 131912141,
+    "9a6fcf69f0930f02b454b42d123ba77868de0180": 132130662,
 }
 
 
