@@ -86,12 +86,13 @@ template <> struct Io<int16_t> {
 };
 
 constexpr int kBufs = 4;        // TMEM ring: [A_hi 32 | A_lo 32 | D 64] columns each
-constexpr int kDcRing = 2 * kBufs;
+                                // (DC ring: twice as deep, Layout::kDcRing)
 
 // S input stages, NS operator slots (1 for a single item, 2 for groups), OB
 // output staging buffers (2; 0 for the pixel output, which stores from
 // registers and spends that shared memory on input stages instead)
-template <typename IoT, int S, int NS, int OB = 2> struct Layout {
+template <typename IoT, int S, int NS, int OB = 2, int NB = kBufs> struct Layout {
+  static constexpr int kDcRing = 2 * NB;
   static constexpr int kStageBytes = kTile * Io<IoT>::kRowBytes;
   static constexpr int kBoxBytes = kTile * 128;              // one 128-row box
   static constexpr int kSlabBytes = 32 * Io<IoT>::kRowBytes; // one warp's output rows
@@ -101,7 +102,7 @@ template <typename IoT, int S, int NS, int OB = 2> struct Layout {
   static constexpr int kOffSlot = kOffOut + OB * kStageBytes;
   static constexpr int kOffDc = kOffSlot + NS * kSlotBytes;
   static constexpr int kOffBar = kOffDc + kDcRing * kTile * 4;
-  static constexpr int kNumBars = 2 * S + 3 * kBufs + kDcRing + 2 * NS;
+  static constexpr int kNumBars = 2 * S + 3 * NB + kDcRing + 2 * NS;
   static constexpr int kOffMisc = kOffBar + kNumBars * 8;
   static constexpr int kSmem = kOffMisc + 16 + 1024;
   static_assert(kSmem <= 232448, "shared memory");
@@ -240,7 +241,22 @@ __device__ __forceinline__ uint32_t pixel_u8_low_byte(float p) {
 // FP32 I/O: at most 152 registers a thread (58,368 of the SM's 65,536 for 384
 // threads), so the small FP64 operator-build kernels of the next image can
 // run on the same SMs while this kernel streams.
-enum : int { kModeBlocks = 0, kModePixels = 1, kModePlanar = 2, kModeHost = 3 };
+enum : int { kModeBlocks = 0, kModePixels = 1, kModePlanar = 2, kModeHost = 3, kModePixelsHalf = 4 };
+
+// kModePixelsHalf: the pixel output of one image in CTAs of half an SM (384
+// threads x 80 registers, two input stages, two TMEM buffers of the ring,
+// 256 columns, ~85 KB of shared memory), two per SM.  One launch of whole-SM
+// CTAs loses its first load's latency and its last tiles' drain, which no
+// CTA of the next launch can fill; with two CTAs an SM, a CTA of the next
+// launch starts on an SM as soon as one of this launch's CTAs there has
+// left, so fills and drains overlap.
+__host__ __device__ constexpr bool is_pixels(int mode) {
+  return mode == kModePixels || mode == kModePixelsHalf;
+}
+__host__ __device__ constexpr int ring_bufs(int mode) { return mode == kModePixelsHalf ? 2 : kBufs; }
+__host__ __device__ constexpr uint32_t ring_cols(int mode) {
+  return mode == kModePixelsHalf ? 256u : kTmemCols;
+}
 
 // The pixel mode runs eight epilogue warps in two sets of four (one warp per
 // TMEM lane quarter), the sets taking alternate tiles, so two tiles' 64
@@ -254,11 +270,17 @@ constexpr int kEpiReleaseThreads = 128;
 __host__ __device__ constexpr int block_threads(int mode) { return 256 + 32 * epi_warps(mode); }
 
 template <typename IoT, int S, int NS, bool kGroup, int kMode>
-__global__ void __maxnreg__(kMode == kModePixels ? 128 : sizeof(IoT) == 4 ? 152 : 168)
+__global__ void __maxnreg__(kMode == kModePixelsHalf ? 80
+                            : kMode == kModePixels ? 128
+                            : sizeof(IoT) == 4 ? 152 : 168)
 apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__ GroupItem single,
                    int nitems, int64_t total_halves, int max_take, int interleaved,
                    uint32_t *__restrict__ err) {
-  using L = Layout<IoT, S, NS, kMode == kModePixels ? 0 : 2>;
+  using L = Layout<IoT, S, NS, is_pixels(kMode) ? 0 : 2, ring_bufs(kMode)>;
+  // the TMEM ring of this mode (these shadow the whole-SM constants)
+  constexpr int kBufs = ring_bufs(kMode);
+  constexpr int kDcRing = L::kDcRing;
+  constexpr uint32_t kTmemCols = ring_cols(kMode);
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -446,6 +468,59 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
           !warp_wait_bounded(&slot_full[k], (t.seg / NS) & 1, s_abort, err, kRoleConv | (it << 8)))
         break;
       if (!warp_wait_bounded(&full_in[s], ps, s_abort, err, kRoleConv | (it << 8))) break;
+      if constexpr (kMode == kModePixelsHalf) {
+        // the same split, 32 inputs at a time (80 registers a thread): box
+        // row 0 is split and stored once A buffer b is free, then box row 1
+        // (the stage is released after it)
+        const uint8_t *st = s_in + s * L::kStageBytes + row * 128;
+        const uint32_t t_a = tmem + lane_base + b * 128;
+        bool ok = true;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float4 q =
+                *reinterpret_cast<const float4 *>(st + h * L::kBoxBytes + ((u ^ (row & 7)) << 4));
+            v[4 * u] = q.x; v[4 * u + 1] = q.y; v[4 * u + 2] = q.z; v[4 * u + 3] = q.w;
+          }
+          if (h == 1) mbar_arrive(&empty_in[s]);
+          if (row >= t.rows) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = 0.f;   // rows past the tile: not stored
+          }
+          if (h == 0) {
+            const float x0 = v[0];
+            v[0] = 0.f;
+            // A buffer b is free once the MMAs of tile it - kBufs completed
+            if (!warp_wait_bounded(&mma_done[b], pb ^ 1, s_abort, err, kRoleConv | (it << 8))) {
+              ok = false;
+              break;
+            }
+            s_dc[r * kTile + row] = x0;
+            mbar_arrive(&dc_full[r]);
+            tc_fence_after();
+          }
+          uint32_t hi[16], lo[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const __half2 h2 = __floats2half2_rn(v[2 * c], v[2 * c + 1]);
+            const float2 hf = __half22float2(h2);
+            const __half2 l2 = __floats2half2_rn(v[2 * c] - hf.x, v[2 * c + 1] - hf.y);
+            hi[c] = *reinterpret_cast<const uint32_t *>(&h2);
+            lo[c] = *reinterpret_cast<const uint32_t *>(&l2);
+          }
+          tmem_st16(t_a + 16 * h, hi);
+          tmem_st16(t_a + 32 + 16 * h, lo);
+        }
+        if (!ok) break;
+        tmem_st_wait();
+        tc_fence_before();
+        mbar_arrive(&a_full[b]);
+        if (t.seg_last) mbar_arrive(&slot_empty[k]);
+        ++it;
+        continue;
+      }
       float v[64];
       const uint8_t *st = s_in + s * L::kStageBytes + row * 128;
       if constexpr (kMode == kModePlanar) {
@@ -537,6 +612,58 @@ apply_group_kernel(const GroupItem *__restrict__ gitems, const __grid_constant__
       if (t.seg_first &&
           !warp_wait_bounded(&slot_full[k], (t.seg / NS) & 1, s_abort, err, kRoleEpi | (it << 8)))
         break;
+      if constexpr (kMode == kModePixelsHalf) {
+        // warp 8 + wr: TMEM lanes 32 wr.. (its blocks), every tile, the 64
+        // pixels of a block in two halves of 32 (80 registers a thread)
+        if (!warp_wait_bounded(&mma_done[b], pb, s_abort, err, kRoleEpi | (it << 8))) break;
+        tc_fence_after();
+        // the DC value is read before D[b] is released
+        if (!warp_wait_bounded(&dc_full[r], pr, s_abort, err, kRoleEpi | (it << 8))) break;
+        const float x0 = s_dc[r * kTile + row];
+        const GroupItem &gi = items[t.item];
+        const float out_scale = gi.out_scale;
+        const int bk = t.row0 + row, bw = (int)gi.bw;
+        const bool live = row < t.rows && bk < gi.nblocks;
+        const int by = bk / bw, bx = bk - by * bw;
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {   // pixel rows 4 hc .. 4 hc + 3
+          uint32_t d[32];
+          tmem_ld32(tmem + lane_base + b * 128 + 64 + 32 * hc, d);
+          if (hc == 1) {
+            tc_fence_before();
+            mbar_arrive(&d_empty[b]);
+          }
+          const float4 *mdc4 =
+              reinterpret_cast<const float4 *>(s_slot + k * kSlotBytes + kSlotPieces) + 8 * hc;
+          float px[32];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float4 md = mdc4[u];
+            px[4 * u] = fmaf(__uint_as_float(d[4 * u]), out_scale, md.x * x0);
+            px[4 * u + 1] = fmaf(__uint_as_float(d[4 * u + 1]), out_scale, md.y * x0);
+            px[4 * u + 2] = fmaf(__uint_as_float(d[4 * u + 2]), out_scale, md.z * x0);
+            px[4 * u + 3] = fmaf(__uint_as_float(d[4 * u + 3]), out_scale, md.w * x0);
+          }
+          if (live) {
+            uint8_t *dst = gi.img + ((int64_t)by * 8 + 4 * hc) * gi.pitch + (int64_t)bx * 8;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              uint32_t w[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const float *a = px + 8 * i + 4 * h;
+                w[h] = __byte_perm(
+                    __byte_perm(pixel_u8_low_byte(a[0]), pixel_u8_low_byte(a[1]), 0x0040),
+                    __byte_perm(pixel_u8_low_byte(a[2]), pixel_u8_low_byte(a[3]), 0x0040), 0x5410);
+              }
+              *reinterpret_cast<uint2 *>(dst + i * gi.pitch) = make_uint2(w[0], w[1]);
+            }
+          }
+        }
+        if (t.seg_last) mbar_arrive(&slot_empty[k]);   // done with this slot's G[:,0]
+        ++it;
+        continue;
+      }
       if constexpr (kMode == kModePixels) {
         // warp 8 + 4 set + wr: TMEM lanes 32 wr.. (its blocks), every output
         // column, tiles it with it % 2 == set (TMEM buffers b of that parity)
@@ -771,9 +898,13 @@ cudaError_t launch_cfg(const GroupItem *d_items, const GroupItem &single, int ni
                        int64_t total_halves, int grid, int max_take, int interleaved,
                        uint32_t *err, cudaStream_t s, bool pdl) {
   auto kern = apply_group_kernel<IoT, S, NS, kGroup, kMode>;
-  constexpr int smem = Layout<IoT, S, NS, kMode == kModePixels ? 0 : 2>::kSmem;
+  constexpr int smem = Layout<IoT, S, NS, is_pixels(kMode) ? 0 : 2, ring_bufs(kMode)>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  if (kMode == kModePixelsHalf) {   // room for two CTAs an SM
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block_threads(kMode));
@@ -834,9 +965,12 @@ cudaError_t launch_apply_pixels(const GroupItem &single, int64_t total_halves, i
   int64_t g = grid > 0 ? grid : 0;
   if (g > total_halves) g = total_halves;
   if (g < 1) g = 1;
-  // four input stages, as for coefficients (six measured slower: 23.6 us)
-  return launch_cfg<float, 4, 1, false, kModePixels>(nullptr, single, 1, total_halves, (int)g, 2,
-                                                     1, err, s, pdl);
+  // two half-SM CTAs an SM, two input stages each, interleaved schedule
+  // (giving the two CTAs of an SM unequal shares, so that their drains fall
+  // apart, measured slower: 16.1-19.0 us against 15.9)
+  g = 2 * g > total_halves ? total_halves : 2 * g;
+  return launch_cfg<float, 2, 1, false, kModePixelsHalf>(nullptr, single, 1, total_halves, (int)g,
+                                                         2, 1, err, s, pdl);
 }
 
 // Image-plane coefficients: the 2-D view of an FP32 array of `height` rows
