@@ -17,6 +17,7 @@ the host cores instead (bounded sample of the same workload).
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -46,7 +47,7 @@ GRAPH_STEPS = 200       # steps per captured graph; the timed loop replays sever
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "9a6fcf69f0930f02b454b42d123ba77868de0180": 132130662,
+    "67ee4d5bf3419b20d6e2699c65f579e6880ffc0d": 131837593,
 }
 
 
@@ -376,18 +377,26 @@ def run_serving(lib, torch, n_requests: int, rates=SERVING_RATES):
             w, a, bnd = masks[r.mask_id]
             preps.append(srv.prepare(ins, outs, [qtabs[sc] for sc in r.q_scale], w, a, bnd))
         tickets = []
-        t0 = time.perf_counter()
-        base = stream[0].arrival_s
-        for i, r in enumerate(stream):
-            if i >= ring:
-                srv.wait(tickets[i - ring])              # free the output ring slot
-            target = t0 + (r.arrival_s - base)
-            while time.perf_counter() < target:
-                pass
-            tickets.append(srv.submit_prepared(preps[i]))
-        for t in tickets[max(0, len(tickets) - ring):]:
-            srv.wait(t)
-        wall = time.perf_counter() - t0
+        # no Python garbage collection during the stream: a collection over
+        # the bench's heap can pause the submitter for milliseconds, and the
+        # burst of late arrivals after it then queues on the HBM budget
+        gc.collect()
+        gc.disable()
+        try:
+            t0 = time.perf_counter()
+            base = stream[0].arrival_s
+            for i, r in enumerate(stream):
+                if i >= ring:
+                    srv.wait(tickets[i - ring])              # free the output ring slot
+                target = t0 + (r.arrival_s - base)
+                while time.perf_counter() < target:
+                    pass
+                tickets.append(srv.submit_prepared(preps[i]))
+            for t in tickets[max(0, len(tickets) - ring):]:
+                srv.wait(t)
+            wall = time.perf_counter() - t0
+        finally:
+            gc.enable()
         st = srv.stats()
         srv.close()
         frames = sum(1 for r in stream if r.kind == "frame")
