@@ -300,6 +300,16 @@ dctf_status dctf_group_create(const dctf_group_item *items, int nitems,
  * work, so it can be captured in a CUDA graph and replayed. */
 dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream);
 
+/* Set the flags of later launches of the group (0 clears them).
+ * DCTF_APPLY_INPUTS_READY: the caller guarantees that every item's input and
+ *   operator are already in place when a launch is queued (not written by
+ *   the kernel queued just before it on the stream, e.g. a launch of this
+ *   group over the same outputs is fine).  The launch then uses programmatic
+ *   stream serialisation: its CTAs start on SMs the previous kernel has left
+ *   and begin reading while that kernel finishes; no output is written
+ *   before the previous kernel has completed.  EINVAL for unknown flags. */
+dctf_status dctf_group_set_flags(dctf_group *g, uint32_t flags);
+
 /* Autotuner: time each candidate (CTA count x tile height x shared-memory
  * layout, i.e. input stages x operator slots) in `reps` rounds of four
  * back-to-back launches on this group (it really runs the group: no item

@@ -63,6 +63,7 @@ _SIGS = {
     "dctf_group_tune": (_i32, [_vp, _vp, _i32]),
     "dctf_group_config": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "dctf_group_set_config": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+    "dctf_group_set_flags": (_i32, [_vp, ctypes.c_uint32]),
     "dctf_group_status": (_i32, [_vp, _vp, _i32]),
     "dctf_group_destroy": (None, [_vp]),
     "dctf_apply_grouped": (_i32, [_vp, _i32, _i32, _vp]),
@@ -302,6 +303,10 @@ class Group:
 
     def set_config(self, grid: int, tile_rows: int, stages: int, slots: int) -> None:
         _check(load().dctf_group_set_config(self.handle, grid, tile_rows, stages, slots))
+
+    def set_flags(self, flags: int) -> None:
+        """APPLY_INPUTS_READY: later launches use programmatic serialisation."""
+        _check(load().dctf_group_set_flags(self.handle, flags))
 
     def status(self, clear: bool = False) -> int:
         code = ctypes.c_uint32(0)

@@ -1024,7 +1024,7 @@ int group_variant_slots(int, int variant) { return variant == 2 ? 1 : 2; }
 
 cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int64_t total_halves,
                                       int grid, int max_take, uint32_t *err, cudaStream_t s,
-                                      int variant) {
+                                      int variant, bool pdl) {
   if (total_halves <= 0) return cudaSuccess;
   int64_t g = grid > 0 ? grid : 0;
   if (g > total_halves) g = total_halves;
@@ -1034,13 +1034,13 @@ cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int6
   switch (variant) {
     case 1:
       return launch_cfg<float, 5, 2, true, kModePixels>(d_items, kEmpty, nitems, total_halves,
-                                                        (int)g, take, 0, err, s, false);
+                                                        (int)g, take, 0, err, s, pdl);
     case 2:
       return launch_cfg<float, 6, 1, true, kModePixels>(d_items, kEmpty, nitems, total_halves,
-                                                        (int)g, take, 0, err, s, false);
+                                                        (int)g, take, 0, err, s, pdl);
     default:
       return launch_cfg<float, 4, 2, true, kModePixels>(d_items, kEmpty, nitems, total_halves,
-                                                        (int)g, take, 0, err, s, false);
+                                                        (int)g, take, 0, err, s, pdl);
   }
 }
 

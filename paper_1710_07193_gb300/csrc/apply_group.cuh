@@ -82,7 +82,7 @@ int group_variant_slots(int kind, int variant);
 // schedule.
 cudaError_t launch_apply_group_pixels(const GroupItem *d_items, int nitems, int64_t total_halves,
                                       int grid, int max_take, uint32_t *err, cudaStream_t s,
-                                      int variant = 0);
+                                      int variant = 0, bool pdl = false);
 
 // Host-direct grouped apply of int16 items (serving): each item's hin/hout
 // are mapped page-locked host buffers, its quantisation tables and operator

@@ -43,6 +43,7 @@ struct dctf_group {
   int max_take;    // 2: 128-row tiles, 1: 64-row tiles
   int variant;     // shared-memory layout (stages x slots), 0..kGroupVariants-1
   bool in_place;   // some item filters in place (tuning would re-filter it)
+  uint32_t flags;  // DCTF_APPLY_INPUTS_READY: launch with programmatic serialisation
 };
 
 namespace dctf {
@@ -206,11 +207,12 @@ dctf_status fill_pixel_items(const dctf_pixel_item *items, int nitems,
 }
 
 cudaError_t launch(const dctf_group *g, int grid, int max_take, int variant, cudaStream_t s) {
+  const bool pdl = (g->flags & DCTF_APPLY_INPUTS_READY) != 0;
   if (g->pixels)
     return launch_apply_group_pixels(g->d_items, g->nitems, g->total_halves, grid, max_take,
-                                     g->d_err, s, variant);
+                                     g->d_err, s, variant, pdl);
   return launch_apply_group(g->d_items, nullptr, g->nitems, g->total_halves, g->i16, grid,
-                            max_take, g->d_err, s, false, variant);
+                            max_take, g->d_err, s, pdl, variant);
 }
 
 // Uploads the descriptors and picks the launch parameters (the autotuner's
@@ -378,6 +380,13 @@ dctf_status dctf_group_set_config(dctf_group *g, int grid, int tile_rows, int st
   g->grid = grid;
   g->max_take = tile_rows / 64;
   g->variant = v;
+  return DCTF_OK;
+}
+
+dctf_status dctf_group_set_flags(dctf_group *g, uint32_t flags) {
+  if (g == nullptr) return set_error(DCTF_EINVAL, "group is NULL");
+  if (flags & ~(uint32_t)DCTF_APPLY_INPUTS_READY) return set_error(DCTF_EINVAL, "unknown flags");
+  g->flags = flags;
   return DCTF_OK;
 }
 

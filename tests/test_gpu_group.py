@@ -275,3 +275,39 @@ def test_tune_cache_persists_across_processes(dctf, tmp_path):
     lines = (tmp_path / "tune.txt").read_text().split("\n")
     assert any(len(ln.split()) == 7 for ln in lines)
     assert run("none") == tuned
+
+
+def test_group_inputs_ready_flag_same_bits(dctf, small_batch):
+    """DCTF_APPLY_INPUTS_READY on a group (programmatic serialisation):
+    several launches back to back, directly and in a graph, give the bits of
+    an ordinary launch; unknown flags are refused."""
+    items, refs = make_items(dctf, small_batch)
+    g = dctf.group_create(items)
+    g.launch()
+    torch.cuda.synchronize()
+    plain = [yd.clone() for _, _, yd, _ in items]
+    g.set_flags(dctf.APPLY_INPUTS_READY)
+    for _, _, yd, _ in items:
+        yd.fill_(float("nan"))
+    for _ in range(4):
+        g.launch()
+    torch.cuda.synchronize()
+    for (_, _, yd, _), p in zip(items, plain):
+        assert torch.equal(yd, p)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            for _ in range(3):
+                g.launch(stream=s)
+    for _, _, yd, _ in items:
+        yd.fill_(float("nan"))
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    for (_, _, yd, _), p in zip(items, plain):
+        assert torch.equal(yd, p)
+    assert g.status() == 0
+    with pytest.raises(dctf.DctfError):
+        g.set_flags(2)
+    g.destroy()
