@@ -525,7 +525,7 @@ def run_grouped(lib, torch, reps: int, out: dict):
     # then the autotuner's choice
     grp.set_config(0, 128, 3, 2)
     t_default = graph_time_ms(torch, lambda s: grp.launch(stream=s), reps)
-    grp.tune(reps=5)
+    grp.tune(reps=9)
     tg = graph_time_ms(torch, lambda s: grp.launch(stream=s), reps)
     ts = graph_time_ms(torch, lambda s: [lib.apply(o, xi, n, yi, stream=s) for o, xi, yi, n in items],
                        max(1, reps // 4))
