@@ -573,10 +573,14 @@ def run_large(lib, torch, reps: int, out: dict):
     # the device, equal to the paper's M to 1e-12) applied in FP64 on the
     # host to a sample of 4096 blocks spread over the image
     m64, _ = op.download()
+    # the input and the operator are in place before every apply: the
+    # tensor-core applies use programmatic stream serialisation
+    op.set_flags(lib.APPLY_INPUTS_READY)
     idx = torch.linspace(0, nb - 1, 4096).long()
     xs64 = xl[idx.to(dev)].double().cpu().numpy()
     ys64 = xs64 @ m64.T
-    res = {"blocks": nb, "error_sample_blocks": 4096}
+    res = {"blocks": nb, "error_sample_blocks": 4096,
+           "launch": "back to back in a CUDA graph, DCTF_APPLY_INPUTS_READY"}
     # pixel-domain error of the same sample: the orthonormal inverse DCT
     # (Eq. 3) of each block's coefficient error, C^T E C
     u = np.arange(16)[:, None]
@@ -597,6 +601,7 @@ def run_large(lib, torch, reps: int, out: dict):
     sep = datagen.gaussian_mask(9, 2.5)
     op = lib.build_operator(sep, job.anchor, 16, job.boundary, kron=True)
     m64, _ = op.download()
+    op.set_flags(lib.APPLY_INPUTS_READY)
     ys64 = xl[idx.to(dev)].double().cpu().numpy() @ m64.T
     for name in ("KRON_FP32", "KRON_F16X3", "F16X3"):
         op.set_precision(getattr(lib, name))

@@ -263,6 +263,9 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  // A launch of this kernel that follows on the stream may be scheduled now
+  // (it only does so when launched for programmatic stream serialisation).
+  if (tid == 0) pdl_launch_dependents();
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
@@ -395,6 +398,11 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
     const int ew = warp - 8, wr = warp & 3, hc = ew >> 2, r32 = lane, row = wr * 32 + lane;
     const uint32_t lane_base = (uint32_t)(wr * 32) << 16;
     constexpr int kJ = kOut / 64;              // 32-column slices per warp
+    // Under programmatic dependent launch the loads may run while the
+    // previous kernel on the stream finishes; no output is written before
+    // that kernel has completed (it may still read the output buffer).
+    if (lane == 0) pdl_wait();
+    __syncwarp();
     for (int it = 0; it < my_tiles; ++it) {
       const int tile = grp + it * ngroups;
       const int r = it % kDcRing, db = it % kDBufs;
@@ -499,7 +507,8 @@ cudaError_t make_map(CUtensorMap *m, const void *ptr, int64_t nblocks, int box_r
 
 template <class S>
 cudaError_t launch(const dctf_operator *op, const void *pieces, float out_scale,
-                   const CUtensorMap &tin, const CUtensorMap &tout, int ntiles, cudaStream_t s) {
+                   const CUtensorMap &tin, const CUtensorMap &tout, int ntiles, cudaStream_t s,
+                   bool pdl) {
   using L = Layout<S>;
   cudaError_t e = cudaFuncSetAttribute(apply_n16_kernel<S>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem);
@@ -507,15 +516,29 @@ cudaError_t launch(const dctf_operator *op, const void *pieces, float out_scale,
   int groups = sm_count(op->device) / L::kParts;
   if (groups > ntiles) groups = ntiles;
   if (groups < 1) groups = 1;
-  apply_n16_kernel<S><<<L::kParts * groups, kThreads, L::kSmem, s>>>(
-      tin, tout, reinterpret_cast<const uint4 *>(pieces), op->d_Mdc, out_scale, ntiles, op->d_err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L::kParts * groups);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = L::kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (pdl) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  e = cudaLaunchKernelEx(&cfg, apply_n16_kernel<S>, tin, tout,
+                         reinterpret_cast<const uint4 *>(pieces), op->d_Mdc, out_scale, ntiles,
+                         op->d_err);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks, float *y,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool pdl) {
   if (op->d_f16 == nullptr || op->d_bf16 == nullptr || op->d_tf32 == nullptr)
     return cudaErrorInvalidValue;
   CUtensorMap tin, tout;
@@ -525,15 +548,15 @@ cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nb
   const int ntiles = (int)((nblocks + kTile - 1) / kTile);
   switch (op->precision) {
     case DCTF_F16X3:
-      return launch<SplitF16x3>(op, op->d_f16, ldexpf(1.0f, -op->f16_scale_exp), tin, tout, ntiles, s);
+      return launch<SplitF16x3>(op, op->d_f16, ldexpf(1.0f, -op->f16_scale_exp), tin, tout, ntiles, s, pdl);
     case DCTF_BF16X6:
-      return launch<SplitBf16x6>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s);
+      return launch<SplitBf16x6>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_TF32X3:
-      return launch<SplitTf32x3>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s);
+      return launch<SplitTf32x3>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_TF32X1:
-      return launch<SplitTf32x1>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s);
+      return launch<SplitTf32x1>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_BF16X3:
-      return launch<SplitBf16x3>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s);
+      return launch<SplitBf16x3>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s, pdl);
     default:
       return cudaErrorInvalidValue;
   }

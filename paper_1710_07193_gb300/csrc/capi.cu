@@ -355,7 +355,8 @@ static dctf_status apply_impl(const dctf_operator *op, const float *coeffs, int6
     if (static_cast<const void *>(coeffs) == static_cast<const void *>(out))
       return set_error(DCTF_EINVAL,
                        "16x16 tensor-core apply cannot run in place (use DCTF_FP32_SIMT)");
-    e = launch_apply_n16(op, coeffs, nblocks, out, stream);
+    e = launch_apply_n16(op, coeffs, nblocks, out, stream,
+                         allow_pdl && (op->flags & DCTF_APPLY_INPUTS_READY) != 0);
   } else {
     // one item of the persistent tensor-core kernel, descriptor by value
     GroupItem gi;

@@ -113,8 +113,10 @@ inline bool tc_supported(int n, dctf_precision p) {
   return n == 16 && (p == DCTF_F16X3 || p == DCTF_BF16X6 || p == DCTF_TF32X1 || p == DCTF_TF32X3 ||
                      p == DCTF_BF16X3);
 }
+// pdl: launch with programmatic stream serialisation (the input and the
+// operator must not be written by the preceding kernel on the stream)
 cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nblocks,
-                             float *y, cudaStream_t s);
+                             float *y, cudaStream_t s, bool pdl);
 
 // kron.cu: the Kronecker (sandwich-product) form of the operator, built on
 // the device (rank split, factors, and for n = 16 the tensor-core pieces)

@@ -430,3 +430,27 @@ def test_inputs_ready_flag(dctf, ragged_source):
     assert torch.equal(y, ref[0])
     op.set_flags(0)
     assert op.status() == 0
+
+
+@pytest.mark.parametrize("prec", ["F16X3", "BF16X6", "TF32X3"])
+def test_n16_inputs_ready_same_bits(dctf, n16_source, prec):
+    """The 16x16 tensor-core applies under DCTF_APPLY_INPUTS_READY
+    (programmatic stream serialisation): applies queued back to back, each
+    writing a different output while the previous one finishes, give the
+    bits of an ordinary launch."""
+    _, x = n16_source
+    x = x[:5000]
+    w, a = datagen.large_mask(), (4, 4)
+    op = dctf.build_operator(w, a, 16, dctf.REPLICATE)
+    y_plain = run(dctf, op, x, getattr(dctf, prec))
+    op.set_flags(dctf.APPLY_INPUTS_READY)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    outs = [torch.full_like(xd, float("nan")) for _ in range(4)]
+    for _ in range(2):
+        for yd in outs:
+            dctf.apply(op, xd, x.shape[0], yd)
+    torch.cuda.synchronize()
+    for yd in outs:
+        assert np.array_equal(yd.cpu().numpy().astype(np.float64), y_plain)
+    assert op.status() == 0
+    op.release()
