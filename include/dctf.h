@@ -158,10 +158,10 @@ dctf_status dctf_operator_set_precision(dctf_operator *op, dctf_precision p);
  *   dctf_apply through this operator, and the operator itself, are already
  *   in place when the apply is queued (not written by the kernel queued
  *   just before it on the stream).  The 8x8 and 16x16 tensor-core applies
- *   are then launched with programmatic stream serialisation: their CTAs
- *   start on SMs the previous kernel has left and begin reading while that
- *   kernel finishes.  No output is written before the previous kernel has
- *   completed.  Ignored by the other kernels. */
+ *   (DCTF_KRON_F16X3 included) are then launched with programmatic stream
+ *   serialisation: their CTAs start on SMs the previous kernel has left and
+ *   begin reading while that kernel finishes.  No output is written before
+ *   the previous kernel has completed.  Ignored by the other kernels. */
 enum { DCTF_APPLY_INPUTS_READY = 1u };
 
 /* Set the DCTF_APPLY_* flags of later dctf_apply calls (0 clears them). */

@@ -348,9 +348,9 @@ static dctf_status apply_impl(const dctf_operator *op, const float *coeffs, int6
     e = launch_apply_kron(op, coeffs, nblocks, out, stream);   // in place is fine: a thread
                                                                // writes only the row it read
   } else if (op->precision == DCTF_KRON_F16X3) {
-    e = launch_apply_kron_tc(op, coeffs, nblocks, out, stream);   // in place is fine: a unit of
-                                                                  // 8 blocks is read before its
-                                                                  // output is written
+    // in place is fine: a unit of 8 blocks is read before its output is written
+    e = launch_apply_kron_tc(op, coeffs, nblocks, out, stream,
+                             allow_pdl && (op->flags & DCTF_APPLY_INPUTS_READY) != 0);
   } else if (op->n == 16) {
     if (static_cast<const void *>(coeffs) == static_cast<const void *>(out))
       return set_error(DCTF_EINVAL,

@@ -126,7 +126,7 @@ cudaError_t launch_apply_kron(const dctf_operator *op, const float *x, int64_t n
                               cudaStream_t s);
 // kron_tc.cu: the sandwich products on tensor cores (n = 16, F16X3)
 cudaError_t launch_apply_kron_tc(const dctf_operator *op, const float *x, int64_t nblocks,
-                                 float *y, cudaStream_t s);
+                                 float *y, cudaStream_t s, bool pdl);
 
 int sm_count(int device);
 

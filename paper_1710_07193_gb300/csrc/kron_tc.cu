@@ -166,6 +166,9 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s_tmem;
+  // A launch of this kernel that follows on the stream may be scheduled now
+  // (it only does so when launched for programmatic stream serialisation).
+  if (tid == 0) pdl_launch_dependents();
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------- producer
@@ -349,6 +352,10 @@ apply_kron_tc_kernel(const __grid_constant__ CUtensorMap tm_in, float *__restric
     float mdc[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) mdc[i] = s_mdc[i * 16 + j];
+    // no output is written before the previous kernel on the stream has
+    // completed (under programmatic dependent launch)
+    if (lane == 0) pdl_wait();
+    __syncwarp();
     for (int k = 0; k < my_units; ++k) {
       const int64_t unit = cta + (int64_t)k * G;
       float acc[16];
@@ -413,7 +420,7 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 cudaError_t launch_apply_kron_tc(const dctf_operator *op, const float *x, int64_t nblocks,
-                                 float *y, cudaStream_t s) {
+                                 float *y, cudaStream_t s, bool pdl) {
   if (op->n != 16 || op->d_kpieces == nullptr || nblocks * 8 >= ((int64_t)1 << 31))
     return cudaErrorInvalidValue;
   EncodeTiledFn enc = encode_fn();
@@ -436,9 +443,22 @@ cudaError_t launch_apply_kron_tc(const dctf_operator *op, const float *x, int64_
   int grid = sm_count(op->device);
   if (grid > nunits) grid = (int)nunits;
   if (grid < 1) grid = 1;
-  apply_kron_tc_kernel<<<grid, kThreads, kSmem, s>>>(
-      tm, y, nblocks, reinterpret_cast<const uint4 *>(op->d_kpieces), op->d_Mdc, op->d_krank,
-      op->d_kscale, op->d_err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (pdl) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  e = cudaLaunchKernelEx(&cfg, apply_kron_tc_kernel, tm, y, nblocks,
+                         reinterpret_cast<const uint4 *>(op->d_kpieces), op->d_Mdc,
+                         op->d_krank, op->d_kscale, op->d_err);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -222,3 +222,24 @@ def test_kron_tc_rebuild_zero_mask_and_support(dctf, tc_source):
         op8.set_precision(dctf.KRON_F16X3)
     assert e.value.status == 6
     op8.release()
+
+
+def test_kron_tc_inputs_ready_same_bits(dctf, tc_source):
+    """DCTF_KRON_F16X3 under DCTF_APPLY_INPUTS_READY (programmatic stream
+    serialisation): applies queued back to back into different outputs give
+    the bits of an ordinary launch."""
+    _, x = tc_source
+    op = dctf.build_operator(datagen.large_mask(), (4, 4), 16, dctf.REPLICATE, kron=True)
+    op.set_precision(dctf.KRON_F16X3)
+    y_plain = run(dctf, op, x)
+    op.set_flags(dctf.APPLY_INPUTS_READY)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    outs = [torch.full_like(xd, float("nan")) for _ in range(4)]
+    for _ in range(2):
+        for yd in outs:
+            dctf.apply(op, xd, x.shape[0], yd)
+    torch.cuda.synchronize()
+    for yd in outs:
+        assert np.array_equal(yd.cpu().numpy().astype(np.float64), y_plain)
+    assert op.status() == 0
+    op.release()
