@@ -37,7 +37,7 @@
 //    128 x kOut x K MMAs into the two accumulators of the tile.
 //  * Output chunks.  Eight epilogue warps, two per TMEM lane quarter, each
 //    reading half of the tile's output columns 32 at a time and TMA-storing
-//    them as 32 x 16 boxes through one 2 KB staging box per warp; two warps per quarter
+//    them as 32 x 8 boxes through one 1 KB staging box per warp; two warps per quarter
 //    halve the time the (single-buffered, for kOut = 128) accumulators are
 //    held after the MMAs (16x16 F16X3: 150 -> 133 us at 8192^2), and each
 //    warp releases them as soon as it has read its slices (-> 128 us).
@@ -103,17 +103,18 @@ constexpr int kDcRing = 8;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kRingCols = 256;      // A ring: columns 0..255; accumulators 256..511
 constexpr int kChunkBytes = kTile * kChunkK * 4;    // 16 KB: one box (32 floats x 128 rows)
-constexpr int kOutSlab = 32 * 64;                   // one warp's 32 x 16 floats box (SWIZZLE_64B)
+constexpr int kOutSlab = 32 * 32;                   // one warp's 32 x 8 floats box (SWIZZLE_32B)
 
 template <class S>
 struct Layout {
   // Input chunks arrive ~2,100 cycles after their TMA load is issued, and a
   // stage is issued again only once the converter has read it, so the
   // chunk rate is stages / (load latency + conversion): the two-CTA splits
-  // (M's 128 output rows resident, 128 KB) fit a fourth stage because each
-  // epilogue warp stages its output in 16-column halves (16x16 F16X3:
-  // 117 -> ~111 us at 8192^2); the four-CTA splits keep three.
-  static constexpr int kStages = S::kOut == 128 ? 4 : 3;
+  // (M's 128 output rows resident, 128 KB) fit five stages because each
+  // epilogue warp stages its output in 32 x 8 quarters through 1 KB (16x16
+  // F16X3 at 8192^2: 117 us with three stages, 109 with four, 94.5 with
+  // five); the four-CTA splits keep three.
+  static constexpr int kStages = S::kOut == 128 ? 5 : 3;
   static constexpr int kElem = S::kTf32 ? 4 : 2;            // bytes per piece element
   static constexpr int kRowElems = 128 / kElem;             // K per 128-byte B row
   static constexpr int kBlocksK = kN2 / kRowElems;          // 128-byte K blocks of B
@@ -430,28 +431,28 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
 #pragma unroll
       for (int jj = 0; jj < kJ; ++jj) {
         const int j = hc * kJ + jj;
-        // two 32 x 16 halves of the slice through the warp's 2 KB box
+        // four 32 x 8 quarters of the slice through the warp's 1 KB box
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
+        for (int hh = 0; hh < 4; ++hh) {
           if (lane == 0) bulk_wait_read<0>();   // the warp's staging box is free
           __syncwarp();
           uint8_t *slab = s_out + ew * kOutSlab;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int uu = 4 * hh + u;
+          for (int u = 0; u < 2; ++u) {
+            const int uu = 2 * hh + u;
             const float4 md = reinterpret_cast<const float4 *>(s_mdc)[8 * j + uu];
             float4 y;
             y.x = fmaf(acc[jj][4 * uu], out_scale, md.x * x0);
             y.y = fmaf(acc[jj][4 * uu + 1], out_scale, md.y * x0);
             y.z = fmaf(acc[jj][4 * uu + 2], out_scale, md.z * x0);
             y.w = fmaf(acc[jj][4 * uu + 3], out_scale, md.w * x0);
-            // SWIZZLE_64B: 16-byte chunk u of 64-byte row r32 at u ^ ((r32 >> 1) & 3)
-            *reinterpret_cast<float4 *>(slab + r32 * 64 + ((u ^ ((r32 >> 1) & 3)) << 4)) = y;
+            // SWIZZLE_32B: 16-byte chunk u of 32-byte row r32 at u ^ ((r32 >> 2) & 1)
+            *reinterpret_cast<float4 *>(slab + r32 * 32 + ((u ^ ((r32 >> 2) & 1)) << 4)) = y;
           }
           fence_async_smem();
           __syncwarp();
           if (lane == 0) {
-            tma_store_2d(&tm_out, slab, part * kOut + 32 * j + 16 * hh, tile * kTile + wr * 32);
+            tma_store_2d(&tm_out, slab, part * kOut + 32 * j + 8 * hh, tile * kTile + wr * 32);
             bulk_commit();
           }
         }
@@ -500,7 +501,9 @@ cudaError_t make_map(CUtensorMap *m, const void *ptr, int64_t nblocks, int box_r
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(ptr), dims, strides,
                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   box_cols == 32   ? CU_TENSOR_MAP_SWIZZLE_128B
+                   : box_cols == 16 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                    : CU_TENSOR_MAP_SWIZZLE_32B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -543,7 +546,7 @@ cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nb
     return cudaErrorInvalidValue;
   CUtensorMap tin, tout;
   cudaError_t e = make_map(&tin, x, nblocks, kTile);
-  if (e == cudaSuccess) e = make_map(&tout, y, nblocks, 32, 16);
+  if (e == cudaSuccess) e = make_map(&tout, y, nblocks, 32, 8);
   if (e != cudaSuccess) return e;
   const int ntiles = (int)((nblocks + kTile - 1) / kTile);
   switch (op->precision) {
