@@ -47,7 +47,7 @@ GRAPH_STEPS = 200       # steps per captured graph; the timed loop replays sever
 # ncu DRAM traffic of one apply launch (dram__bytes_read.sum + write.sum) on
 # the full workload, valid only for the kernel source it was taken from.
 NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
-    "67ee4d5bf3419b20d6e2699c65f579e6880ffc0d": 131837593,
+    "3db8aa7b6ecbf2115b830c73bab183696be4d4cc": 131889100,
 }
 
 
