@@ -304,8 +304,9 @@ dctf_status dctf_group_launch(const dctf_group *g, dctf_stream_t stream);
 /* Set the flags of later launches of the group (0 clears them).
  * DCTF_APPLY_INPUTS_READY: the caller guarantees that every item's input and
  *   operator are already in place when a launch is queued (not written by
- *   the kernel queued just before it on the stream, e.g. a launch of this
- *   group over the same outputs is fine).  The launch then uses programmatic
+ *   the kernel queued just before it on the stream: launching a group whose
+ *   items are not in place twice in a row is fine, one with an in-place
+ *   item is not).  The launch then uses programmatic
  *   stream serialisation: its CTAs start on SMs the previous kernel has left
  *   and begin reading while that kernel finishes; no output is written
  *   before the previous kernel has completed.  EINVAL for unknown flags. */
