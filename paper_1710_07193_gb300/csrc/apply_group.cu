@@ -33,7 +33,9 @@
 //    K^T M = H K^T, Eq. 3 applied after Eq. 7); the epilogue rounds half
 //    away from zero, saturates to [0, 255] and writes the block's 8 x 8
 //    bytes into the image (Sec. III's conversion), 64 B per block instead
-//    of 256 B of coefficients.
+//    of 256 B of coefficients.  One image goes through kModePixelsHalf:
+//    the same arithmetic in CTAs of half an SM, two per SM, so a CTA of the
+//    next launch fills an SM while the other CTA there drains.
 //  * Image-plane layout (kMode = kModePlanar): the coefficients of block
 //    (by, bx) sit at rows 8 by + u, columns 8 bx + v of an image-shaped FP32
 //    array (the layout of a JPEG decoder's coefficient plane).  A 2-D TMA
@@ -53,11 +55,13 @@
 // Roles (384 threads; 512 in the pixel mode): warp 0 TMA producer, warp 1
 // MMA issuer, warp 2 TMEM allocator, warp 3 slot loader, warps 4-7
 // converter (thread = tile row), warps 8-11 epilogue (each warp stores its
-// own 32 rows; the pixel mode adds warps 12-15, each pair of warps of a
-// lane quarter splitting a block's pixel rows).  TMEM holds a ring
-// of four [A_hi 32 | A_lo 32 | D 64] column buffers, so the MMA can run up to
+// own 32 rows; the pixel mode adds warps 12-15, the two sets of four taking
+// alternate tiles).  TMEM holds a ring of four [A_hi 32 | A_lo 32 | D 64]
+// column buffers (two in the half-SM pixel mode), so the MMA can run up to
 // four tiles ahead of the epilogue, which frees its buffer right after one
-// paired TMEM load.  Every wait is bounded (see sm100_ptx.cuh); waits in
+// paired TMEM load.  Launched for programmatic stream serialisation, a CTA
+// lets the next launch be scheduled once it is set up, and its epilogue
+// writes nothing before the previous kernel has completed.  Every wait is bounded (see sm100_ptx.cuh); waits in
 // multi-lane roles are warp-uniform.
 #include "apply_group.cuh"
 
