@@ -19,7 +19,10 @@
 // Tensor-core FP32 accumulation truncates, so the order matters: per K half
 // of 128 inputs, each with its own accumulator, the correction products go
 // in first (while the accumulator is small), the main product x_0 m_0 last;
-// the epilogue adds the two halves with round-to-nearest.
+// the epilogue adds the two halves with round-to-nearest.  BF16X6 instead
+// keeps one accumulator per order i + j of its products (SplitBf16x6S
+// below): each holds terms of one magnitude, so no order is needed, and its
+// pieces stack into 3 wider MMAs per K step instead of 6.
 //
 // What 16x16 changes against the 8x8 kernel (apply_group.cu) is size: M is
 // 256 x 256, its pieces 256-512 KB, more than one SM's shared memory, and a
@@ -37,9 +40,10 @@
 //    128 x kOut x K MMAs into the two accumulators of the tile.
 //  * Output chunks.  Eight epilogue warps, two per TMEM lane quarter, each
 //    reading half of the tile's output columns 32 at a time and TMA-storing
-//    them as 32 x 8 boxes through one 1 KB staging box per warp; two warps per quarter
-//    halve the time the (single-buffered, for kOut = 128) accumulators are
-//    held after the MMAs (16x16 F16X3: 150 -> 133 us at 8192^2), and each
+//    them as 32 x 8 boxes through one 1 KB staging box per warp; two warps
+//    per quarter halve the time the (single-buffered, for kOut = 128)
+//    accumulators are held after the MMAs (16x16 F16X3: 150 -> 133 us at
+//    8192^2), and each
 //    warp releases them as soon as it has read its slices (-> 128 us).
 //
 // Roles (512 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM
@@ -63,31 +67,39 @@ using namespace ptx;
 struct SplitF16x3 {
   static constexpr int kPieces = 2, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 2;
   static constexpr bool kTf32 = false, kBf16 = false;
+  static constexpr bool kStacked = false;
   __device__ static constexpr int corr_x(int j) { return j; }
   __device__ static constexpr int corr_m(int j) { return 1 - j; }
-};
-struct SplitBf16x6 {
-  static constexpr int kPieces = 3, kImgPieces = 3, kOut = 64, kDBufs = 2, kCorr = 5;
-  static constexpr bool kTf32 = false, kBf16 = true;
-  // (0,2) (1,1) (2,0) (0,1) (1,0): second-order terms before first-order
-  __device__ static constexpr int corr_x(int j) { return j < 3 ? j : j - 3; }
-  __device__ static constexpr int corr_m(int j) { return j < 3 ? 2 - j : 4 - j; }
 };
 struct SplitTf32x3 {
   static constexpr int kPieces = 2, kImgPieces = 2, kOut = 64, kDBufs = 2, kCorr = 2;
   static constexpr bool kTf32 = true, kBf16 = false;
+  static constexpr bool kStacked = false;
   __device__ static constexpr int corr_x(int j) { return j; }
   __device__ static constexpr int corr_m(int j) { return 1 - j; }
 };
 struct SplitBf16x3 {     // the first two BF16X6 pieces of M
   static constexpr int kPieces = 2, kImgPieces = 3, kOut = 128, kDBufs = 1, kCorr = 2;
   static constexpr bool kTf32 = false, kBf16 = true;
+  static constexpr bool kStacked = false;
   __device__ static constexpr int corr_x(int j) { return j; }
   __device__ static constexpr int corr_m(int j) { return 1 - j; }
+};
+// Stacked form of BF16X6: the products x_i m_j go into one accumulator per
+// order i + j (1, 2^-8, 2^-16 of the result), each holding terms of one
+// magnitude, so chunks need no ordering and a two-chunk A ring suffices; M's
+// three pieces are stacked along N in each K block, so x_i [m_0 | ... |
+// m_(2-i)] is one MMA of N = (3 - i) 64: 3 MMAs per K step instead of 6.
+// Accumulator columns of a tile: [order 0 | order 1 | order 2].
+struct SplitBf16x6S {
+  static constexpr int kPieces = 3, kImgPieces = 3, kOut = 64, kDBufs = 2;
+  static constexpr bool kTf32 = false, kBf16 = true;
+  static constexpr bool kStacked = true;
 };
 struct SplitTf32x1 {
   static constexpr int kPieces = 1, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 0;
   static constexpr bool kTf32 = true, kBf16 = false;
+  static constexpr bool kStacked = false;
   __device__ static constexpr int corr_x(int) { return 0; }
   __device__ static constexpr int corr_m(int) { return 0; }
 };
@@ -120,7 +132,11 @@ struct Layout {
   static constexpr int kBlocksK = kN2 / kRowElems;          // 128-byte K blocks of B
   static constexpr int kPieceCols = kChunkK * kElem / 4;    // TMEM columns per A piece per chunk
   static constexpr int kABufCols = S::kPieces * kPieceCols;
-  static constexpr int kABufs = kRingCols / kABufCols;
+  // accumulator columns a tile: two K halves of kOut, or (stacked) one of
+  // kOut per order; the A ring takes the rest of TMEM
+  static constexpr int kAccCols = S::kStacked ? S::kPieces * S::kOut : kGroups * S::kOut;
+  static constexpr uint32_t kRing = kTmemCols - S::kDBufs * kAccCols;
+  static constexpr int kABufs = kRing / kABufCols;
   static constexpr int kKStep = S::kTf32 ? 8 : 16;          // K per MMA
   static constexpr int kParts = kN2 / S::kOut;
   static constexpr int kBBlock = S::kOut * 128;             // one (piece, K block) of B
@@ -135,8 +151,9 @@ struct Layout {
   static constexpr int kOffMisc = kOffBar + kNumBars * 8;
   static constexpr int kSmem = kOffMisc + 16 + 1024;
   static_assert(kSmem <= 232448, "shared memory");
-  static_assert(kABufs >= kChunks / kGroups, "a K half's chunks must fit the A ring");
-  static_assert(S::kDBufs * kGroups * S::kOut == (int)(kTmemCols - kRingCols), "TMEM split");
+  static_assert(S::kStacked ? kABufs >= 2 : kABufs >= kChunks / kGroups,
+                "a K half's chunks must fit the A ring");
+  static_assert(S::kStacked || kRing == kRingCols, "TMEM split");
   static_assert(kDcRing >= S::kDBufs + 2, "DC ring depth");
   static_assert(!(S::kTf32 && S::kBf16), "one piece type");
 };
@@ -205,6 +222,16 @@ __device__ __forceinline__ void convert_store(const float (&v)[32], uint32_t t_a
     tmem_st16(t_a, hi);
     tmem_st16(t_a + 16, lo);
   }
+}
+
+// Stacked splits: x_i [m_0 | ... | m_(P-1-i)], N = (P - i) kOut.
+template <class S, int I>
+__device__ __forceinline__ void mma_stacked(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
+  constexpr int kN = (S::kPieces - I) * S::kOut;
+  if constexpr (S::kTf32)
+    mma_tf32_ts(d, a, b, idesc_tf32(128, kN), acc);
+  else
+    mma_f16_ts(d, a, b, idesc_f16(128, kN, S::kBf16), acc);
 }
 
 template <class S>
@@ -278,7 +305,9 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
     // thread-by-thread copy before the roles start cost ~7 us a launch.)
     mbar_arrive_expect_tx(b_full, L::kBBytes);
     for (int blk = 0; blk < S::kPieces * L::kBlocksK; ++blk) {
-      const int piece = blk / L::kBlocksK, kb = blk % L::kBlocksK;
+      // piece-major blocks; stacked: K-block-major, the pieces adjacent
+      const int piece = S::kStacked ? blk % S::kPieces : blk / L::kBlocksK;
+      const int kb = S::kStacked ? blk / S::kPieces : blk % L::kBlocksK;
       const size_t src_row0 = (size_t)kb * S::kImgPieces * kN2 + piece * kN2 + part * kOut;
       bulk_load(s_b + blk * L::kBBlock, pieces + src_row0 * 8, L::kBBlock, b_full);
     }
@@ -307,6 +336,38 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
     int q = 0, last_q = -1;
     if (my_tiles > 0 && !wait_bounded(b_full, 0, s_abort, err, kRoleMma))
       goto mma_done_label;
+    if constexpr (S::kStacked) {
+      // Tile t: the accumulator of order o (columns o kOut ..) gets every
+      // x_i m_j with i + j = o, chunk by chunk; a chunk's A buffer is
+      // released after its MMAs
+      for (int it = 0; it < my_tiles; ++it) {
+        const int db = it % kDBufs;
+        if (!wait_bounded(&d_empty[db], ((it / kDBufs) & 1) ^ 1, s_abort, err,
+                          kRoleMma | (it << 8)))
+          goto mma_done_label;
+        const uint32_t t_d = tmem + L::kRing + db * L::kAccCols;
+        for (int kc = 0; kc < kChunks; ++kc, ++q) {
+          const int a = q % kABufs;
+          if (!wait_bounded(&a_full[a], (q / kABufs) & 1, s_abort, err, kRoleMma | (q << 8)))
+            goto mma_done_label;
+          tc_fence_after();
+          const uint32_t t_a = tmem + a * L::kABufCols;
+          const int kb = kc * kChunkK / L::kRowElems;
+          const int kofs = (kc * kChunkK % L::kRowElems) * L::kElem / 16;   // 16-byte units
+          // K block kb: the pieces' kOut rows stacked, m_0 first
+          const uint64_t b = desc_sw128(smem_u32(s_b + kb * S::kPieces * L::kBBlock)) + kofs;
+#pragma unroll
+          for (int kk = 0; kk < kChunkK / L::kKStep; ++kk) {
+            mma_stacked<S, 0>(t_d, t_a + 8 * kk, b + 2 * kk, (kc > 0 || kk > 0) ? 1u : 0u);
+            mma_stacked<S, 1>(t_d + kOut, t_a + L::kPieceCols + 8 * kk, b + 2 * kk, 1u);
+            mma_stacked<S, 2>(t_d + 2 * kOut, t_a + 2 * L::kPieceCols + 8 * kk, b + 2 * kk, 1u);
+          }
+          tc_commit(&a_done[a]);
+          last_q = q;
+        }
+        tc_commit(&d_full[db]);
+      }
+    } else {
     for (int it = 0; it < my_tiles; ++it) {
       const int db = it % kDBufs;
       if (!wait_bounded(&d_empty[db], ((it / kDBufs) & 1) ^ 1, s_abort, err, kRoleMma | (it << 8)))
@@ -349,6 +410,7 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
       }
       q += kChunks;
       tc_commit(&d_full[db]);
+    }
     }
   mma_done_label:
     if (last_q >= 0) wait_drain(&a_done[last_q % kABufs], (last_q / kABufs) & 1, err, kRoleDrain);
@@ -413,18 +475,28 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
       if (!warp_wait_bounded(&dc_full[r], (it / kDcRing) & 1, s_abort, err, kRoleEpi | (it << 8)))
         break;
       const float x0 = s_dc[r * kTile + row];
-      const uint32_t t_d = tmem + lane_base + kRingCols + db * kGroups * kOut;
-      // read this warp's slices of both K-half accumulators and add them,
-      // then release D before staging and storing, so the next tile's MMAs
-      // need not wait for the stores (16x16 F16X3: 135 -> 128 us at 8192^2)
+      const uint32_t t_d = tmem + lane_base + L::kRing + db * L::kAccCols;
+      // read this warp's slices of both K-half accumulators (stacked: of
+      // every order, the smallest first) and add them, then release D before
+      // staging and storing, so the next tile's MMAs need not wait for the
+      // stores (16x16 F16X3: 135 -> 128 us at 8192^2)
       float acc[kJ][32];
 #pragma unroll
       for (int jj = 0; jj < kJ; ++jj) {
         const int j = hc * kJ + jj;
         uint32_t d0[32], d1[32];
-        tmem_ld32x2(t_d + 32 * j, t_d + kOut + 32 * j, d0, d1);
+        if constexpr (S::kStacked) {
+          tmem_ld32x2(t_d + 2 * kOut + 32 * j, t_d + kOut + 32 * j, d0, d1);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[jj][c] = __uint_as_float(d0[c]) + __uint_as_float(d1[c]);
+          for (int c = 0; c < 32; ++c) acc[jj][c] = __uint_as_float(d0[c]) + __uint_as_float(d1[c]);
+          tmem_ld32(t_d + 32 * j, d0);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[jj][c] += __uint_as_float(d0[c]);
+        } else {
+          tmem_ld32x2(t_d + 32 * j, t_d + kOut + 32 * j, d0, d1);
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[jj][c] = __uint_as_float(d0[c]) + __uint_as_float(d1[c]);
+        }
       }
       tc_fence_before();
       mbar_arrive(&d_empty[db]);               // this warp's columns of D have been read
@@ -553,7 +625,7 @@ cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nb
     case DCTF_F16X3:
       return launch<SplitF16x3>(op, op->d_f16, ldexpf(1.0f, -op->f16_scale_exp), tin, tout, ntiles, s, pdl);
     case DCTF_BF16X6:
-      return launch<SplitBf16x6>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s, pdl);
+      return launch<SplitBf16x6S>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_TF32X3:
       return launch<SplitTf32x3>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_TF32X1:
