@@ -43,8 +43,8 @@
 //    them as 32 x 8 boxes through one 1 KB staging box per warp; two warps
 //    per quarter halve the time the (single-buffered, for kOut = 128)
 //    accumulators are held after the MMAs (16x16 F16X3: 150 -> 133 us at
-//    8192^2), and each
-//    warp releases them as soon as it has read its slices (-> 128 us).
+//    8192^2), and each warp releases them as soon as it has read its slices
+//    (-> 128 us).
 //
 // Roles (512 threads): warp 0 TMA producer, warp 1 MMA issuer, warp 2 TMEM
 // allocator, warps 4-7 converter (thread = tile row), warps 8-15 epilogue.
