@@ -94,6 +94,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_bf16_tflops():
+    """(burst, sustained) dense BF16 TFLOP/s of this machine's GPUs, and whether
+    they are the measured figures or the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    return 1900.0, 1700.0, "fallback"
+
+
 def kernel_source_hash():
     with open(os.path.join(ROOT, "paper_1710_07193_gb300", "csrc", "apply_group.cu"), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
@@ -642,6 +653,17 @@ def headline_keys(simt, apply_mean_ms, pixels, planar, serving, e2e, workloads=N
         out["n16_8192"] = {k: _r(L[k]["us"]) for k in ("F16X3", "BF16X6", "TF32X3", "FP32_SIMT",
                                                         "KRON_F16X3", "separable_9x9_KRON_F16X3",
                                                         "separable_9x9_F16X3")}
+        # F16X3 against HBM (2 KB a block); BF16X6 against the BF16 tensor
+        # rate (six 256 x 256 products a block, 2 flops a multiply-add)
+        nb16 = L["blocks"]
+        burst, sustained, kind = measured_bf16_tflops()
+        bf6 = 6 * 2 * 256 * 256 * nb16 / (L["BF16X6"]["us"] * 1e-6) / 1e12
+        out["n16_8192"]["F16X3_hbm_frac"] = _r(nb16 * 2048 / (L["F16X3"]["us"] * 1e-6) / 1e9
+                                               / measured_peaks()[0], 3)
+        out["n16_8192"]["BF16X6_tflops"] = _r(bf6)
+        out["n16_8192"]["BF16X6_tensor_frac"] = {"of_burst": _r(bf6 / burst, 3),
+                                                 "of_sustained": _r(bf6 / sustained, 3),
+                                                 "peaks": kind}
     if simt is not None:
         out["fp32_simt"] = {"apply_us": _r(simt["apply_us"]), "f16x3_apply_us": _r(1e3 * apply_mean_ms),
                             "f16x3_speedup": _r(simt["apply_us"] / (1e3 * apply_mean_ms), 3),
