@@ -79,6 +79,23 @@ def test_pitch_padding_untouched_and_inputs_ready(dctf):
     op.release()
 
 
+@pytest.mark.parametrize("hw", [(1024, 1024), (2048, 1536)])
+def test_pixels_one_cta_per_sm_under_inputs_ready(dctf, hw):
+    """With DCTF_APPLY_INPUTS_READY an image of up to 2,048 half tiles goes
+    out with one CTA an SM (two otherwise): the same pixels either way, and
+    the oracle's."""
+    h, wd = hw
+    img = datagen.synthetic_image(h, wd, datagen.rng(97, 102, h))
+    w, a = datagen.headline_mask(), (1, 3)
+    op = dctf.build_operator(w, a, 8, dctf.REPLICATE)
+    u8, _ = run_pixels(dctf, op, img)
+    u8b, _ = run_pixels(dctf, op, img, flags=dctf.APPLY_INPUTS_READY)
+    assert np.array_equal(u8, u8b)
+    check_image(u8b, img, w, a, oracle.REPLICATE)
+    assert op.status() == 0
+    op.release()
+
+
 def test_pixels_agree_with_coefficient_route(dctf):
     """The fused kernel and dctf_apply followed by the inverse DCT give the
     same uint8 image outside the tie band (two device routes, one result)."""
