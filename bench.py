@@ -50,6 +50,9 @@ NCU_TRAFFIC = {               # {sha1 of apply_group.cu: bytes per launch}
     # (captured on 3db8aa7b..., the same code: that source and this one
     # differ in the file's header comment only)
     "282c582d83b8d565e8e19066b3a24970a6fd2e63": 131889100,
+    # the same kernel code: this source differs from the one above only in
+    # the host-side grid choice of the single-image pixel launch
+    "0c94fe2b0ac26a8967b9a560f8bdbc73098ecdae": 131889100,
 }
 
 
