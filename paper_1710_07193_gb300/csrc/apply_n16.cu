@@ -22,7 +22,9 @@
 // the epilogue adds the two halves with round-to-nearest.  BF16X6 instead
 // keeps one accumulator per order i + j of its products (SplitBf16x6S
 // below): each holds terms of one magnitude, so no order is needed, and its
-// pieces stack into 3 wider MMAs per K step instead of 6.
+// pieces stack into 3 wider MMAs per K step instead of 6.  TF32X3 does the
+// same with its order 0 still split by K half (SplitTf32x3S): 2 MMAs per K
+// step instead of 3.
 //
 // What 16x16 changes against the 8x8 kernel (apply_group.cu) is size: M is
 // 256 x 256, its pieces 256-512 KB, more than one SM's shared memory, and a
@@ -67,21 +69,14 @@ using namespace ptx;
 struct SplitF16x3 {
   static constexpr int kPieces = 2, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 2;
   static constexpr bool kTf32 = false, kBf16 = false;
-  static constexpr bool kStacked = false;
-  __device__ static constexpr int corr_x(int j) { return j; }
-  __device__ static constexpr int corr_m(int j) { return 1 - j; }
-};
-struct SplitTf32x3 {
-  static constexpr int kPieces = 2, kImgPieces = 2, kOut = 64, kDBufs = 2, kCorr = 2;
-  static constexpr bool kTf32 = true, kBf16 = false;
-  static constexpr bool kStacked = false;
+  static constexpr bool kStacked = false, kHalvedOrder0 = false;
   __device__ static constexpr int corr_x(int j) { return j; }
   __device__ static constexpr int corr_m(int j) { return 1 - j; }
 };
 struct SplitBf16x3 {     // the first two BF16X6 pieces of M
   static constexpr int kPieces = 2, kImgPieces = 3, kOut = 128, kDBufs = 1, kCorr = 2;
   static constexpr bool kTf32 = false, kBf16 = true;
-  static constexpr bool kStacked = false;
+  static constexpr bool kStacked = false, kHalvedOrder0 = false;
   __device__ static constexpr int corr_x(int j) { return j; }
   __device__ static constexpr int corr_m(int j) { return 1 - j; }
 };
@@ -94,12 +89,25 @@ struct SplitBf16x3 {     // the first two BF16X6 pieces of M
 struct SplitBf16x6S {
   static constexpr int kPieces = 3, kImgPieces = 3, kOut = 64, kDBufs = 2;
   static constexpr bool kTf32 = false, kBf16 = true;
-  static constexpr bool kStacked = true;
+  static constexpr bool kStacked = true, kHalvedOrder0 = false;
+};
+// Stacked form of TF32X3 with order 0 split by K half, since one order-0
+// accumulator over all 256 inputs (32 truncating MMA additions) missed the
+// error bar.  Accumulator columns of a tile: [order 0, K half 0 | order 1 |
+// order 0, K half 1].  M's two pieces are stacked along N in each K block,
+// [m_hi | m_lo] in the first K half and [m_lo | m_hi] in the second, so
+// x_hi against both is one MMA of N = 128 into [A0 | O1], then [O1 | A1];
+// x_lo m_hi is one of N = 64 into O1.  One accumulator set leaves TMEM a
+// five-chunk A ring.
+struct SplitTf32x3S {
+  static constexpr int kPieces = 2, kImgPieces = 2, kOut = 64, kDBufs = 1;
+  static constexpr bool kTf32 = true, kBf16 = false;
+  static constexpr bool kStacked = true, kHalvedOrder0 = true;
 };
 struct SplitTf32x1 {
   static constexpr int kPieces = 1, kImgPieces = 2, kOut = 128, kDBufs = 1, kCorr = 0;
   static constexpr bool kTf32 = true, kBf16 = false;
-  static constexpr bool kStacked = false;
+  static constexpr bool kStacked = false, kHalvedOrder0 = false;
   __device__ static constexpr int corr_x(int) { return 0; }
   __device__ static constexpr int corr_m(int) { return 0; }
 };
@@ -134,7 +142,8 @@ struct Layout {
   static constexpr int kABufCols = S::kPieces * kPieceCols;
   // accumulator columns a tile: two K halves of kOut, or (stacked) one of
   // kOut per order; the A ring takes the rest of TMEM
-  static constexpr int kAccCols = S::kStacked ? S::kPieces * S::kOut : kGroups * S::kOut;
+  static constexpr int kAccCols =
+      S::kStacked ? (S::kHalvedOrder0 ? 3 : S::kPieces) * S::kOut : kGroups * S::kOut;
   static constexpr uint32_t kRing = kTmemCols - S::kDBufs * kAccCols;
   static constexpr int kABufs = kRing / kABufCols;
   static constexpr int kKStep = S::kTf32 ? 8 : 16;          // K per MMA
@@ -234,6 +243,14 @@ __device__ __forceinline__ void mma_stacked(uint32_t d, uint32_t a, uint64_t b, 
     mma_f16_ts(d, a, b, idesc_f16(128, kN, S::kBf16), acc);
 }
 
+template <class S, int N>
+__device__ __forceinline__ void mma_n(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
+  if constexpr (S::kTf32)
+    mma_tf32_ts(d, a, b, idesc_tf32(128, N), acc);
+  else
+    mma_f16_ts(d, a, b, idesc_f16(128, N, S::kBf16), acc);
+}
+
 template <class S>
 __device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
   if constexpr (S::kTf32)
@@ -306,8 +323,12 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
     mbar_arrive_expect_tx(b_full, L::kBBytes);
     for (int blk = 0; blk < S::kPieces * L::kBlocksK; ++blk) {
       // piece-major blocks; stacked: K-block-major, the pieces adjacent
-      const int piece = S::kStacked ? blk % S::kPieces : blk / L::kBlocksK;
       const int kb = S::kStacked ? blk / S::kPieces : blk % L::kBlocksK;
+      // (halved order 0: the pieces in reverse order in the second K half)
+      const int slot = blk % S::kPieces;
+      const int piece = !S::kStacked ? blk / L::kBlocksK
+                        : (S::kHalvedOrder0 && kb >= L::kBlocksK / 2) ? S::kPieces - 1 - slot
+                                                                       : slot;
       const size_t src_row0 = (size_t)kb * S::kImgPieces * kN2 + piece * kN2 + part * kOut;
       bulk_load(s_b + blk * L::kBBlock, pieces + src_row0 * 8, L::kBBlock, b_full);
     }
@@ -355,12 +376,32 @@ apply_n16_kernel(const __grid_constant__ CUtensorMap tm_in, const __grid_constan
           const int kb = kc * kChunkK / L::kRowElems;
           const int kofs = (kc * kChunkK % L::kRowElems) * L::kElem / 16;   // 16-byte units
           // K block kb: the pieces' kOut rows stacked, m_0 first
-          const uint64_t b = desc_sw128(smem_u32(s_b + kb * S::kPieces * L::kBBlock)) + kofs;
+          const uint32_t s_blk = smem_u32(s_b + kb * S::kPieces * L::kBBlock);
+          const uint64_t b = desc_sw128(s_blk) + kofs;
+          if constexpr (S::kHalvedOrder0) {
+            // K half 0: B = [m_hi | m_lo] -> [A0 | O1]; half 1: [m_lo | m_hi] -> [O1 | A1]
+            const bool h1 = kc >= kChunks / 2;
+            const uint64_t b_second = desc_sw128(s_blk + L::kBBlock) + kofs;
+            const uint64_t b_mhi = h1 ? b_second : b;
 #pragma unroll
-          for (int kk = 0; kk < kChunkK / L::kKStep; ++kk) {
-            mma_stacked<S, 0>(t_d, t_a + 8 * kk, b + 2 * kk, (kc > 0 || kk > 0) ? 1u : 0u);
-            mma_stacked<S, 1>(t_d + kOut, t_a + L::kPieceCols + 8 * kk, b + 2 * kk, 1u);
-            mma_stacked<S, 2>(t_d + 2 * kOut, t_a + 2 * L::kPieceCols + 8 * kk, b + 2 * kk, 1u);
+            for (int kk = 0; kk < kChunkK / L::kKStep; ++kk) {
+              if (kc == kChunks / 2 && kk == 0) {
+                // A1 starts here while O1 goes on: the pair as two MMAs
+                mma_n<S, kOut>(t_d + kOut, t_a, b, 1u);                 // x_hi m_lo -> O1
+                mma_n<S, kOut>(t_d + 2 * kOut, t_a, b_second, 0u);      // x_hi m_hi -> A1
+              } else {
+                mma_n<S, 2 * kOut>(h1 ? t_d + kOut : t_d, t_a + 8 * kk, b + 2 * kk,
+                                   (kc > 0 || kk > 0) ? 1u : 0u);
+              }
+              mma_n<S, kOut>(t_d + kOut, t_a + L::kPieceCols + 8 * kk, b_mhi + 2 * kk, 1u);
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < kChunkK / L::kKStep; ++kk) {
+              mma_stacked<S, 0>(t_d, t_a + 8 * kk, b + 2 * kk, (kc > 0 || kk > 0) ? 1u : 0u);
+              mma_stacked<S, 1>(t_d + kOut, t_a + L::kPieceCols + 8 * kk, b + 2 * kk, 1u);
+              mma_stacked<S, 2>(t_d + 2 * kOut, t_a + 2 * L::kPieceCols + 8 * kk, b + 2 * kk, 1u);
+            }
           }
           tc_commit(&a_done[a]);
           last_q = q;
@@ -627,7 +668,7 @@ cudaError_t launch_apply_n16(const dctf_operator *op, const float *x, int64_t nb
     case DCTF_BF16X6:
       return launch<SplitBf16x6S>(op, op->d_bf16, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_TF32X3:
-      return launch<SplitTf32x3>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s, pdl);
+      return launch<SplitTf32x3S>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_TF32X1:
       return launch<SplitTf32x1>(op, op->d_tf32, 1.0f, tin, tout, ntiles, s, pdl);
     case DCTF_BF16X3:
